@@ -1,0 +1,43 @@
+/*
+ * boys_microbench.h -- throughput microbenchmarks used to build the ALU
+ * roofline of the Boys kernels (how fast this GPU retires each FP64/FP32
+ * operation the method of Sec. 2 uses: fused multiply-add, exponential,
+ * square root, reciprocal square root, division).  Not part of the
+ * evaluation path; the paper has no counterpart.
+ */
+#ifndef BOYS_GB300_MICROBENCH_H
+#define BOYS_GB300_MICROBENCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    BOYS_MICRO_DFMA = 0,  /* double fma */
+    BOYS_MICRO_DEXP = 1,  /* double exp (plus one add) */
+    BOYS_MICRO_DSQRT = 2, /* double sqrt (plus one add) */
+    BOYS_MICRO_DRSQRT = 3,/* double rsqrt (plus one add) */
+    BOYS_MICRO_DDIV = 4,  /* double division (plus one add) */
+    BOYS_MICRO_FFMA = 5,  /* float fma */
+    BOYS_MICRO_FEXP2 = 6, /* float exp2f (plus one add) */
+    BOYS_MICRO_FSQRT = 7, /* float sqrtf (plus one add) */
+    BOYS_MICRO_FDIV = 8,  /* float division (plus one add) */
+    BOYS_MICRO_FRSQRT = 9 /* float rsqrtf (plus one add) */
+};
+
+/* Launch `blocks` x 256 threads, each running `iters` iterations of
+ * boys_microbench_ops_per_thread_iter() independent operations of kind `op`
+ * on `stream` (a cudaStream_t as void*).  `sink` is a device double that is
+ * never actually written.  Returns a boys_status. */
+int boys_microbench_launch(int op, int64_t iters, double *sink, int blocks, void *stream);
+
+/* Independent operations per thread and iteration (the chain count). */
+int boys_microbench_ops_per_thread_iter(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,0 +1,71 @@
+// Shared device/host helpers of the Boys-function library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/boys.h"
+
+namespace boys {
+
+// Integer power by repeated squaring, unrolled at compile time.
+template <int K, typename T>
+__device__ __forceinline__ T ipow(T a) {
+  if constexpr (K == 0) {
+    return T(1);
+  } else if constexpr (K == 1) {
+    return a;
+  } else {
+    const T h = ipow<K / 2>(a);
+    if constexpr (K % 2) {
+      return h * h * a;
+    } else {
+      return h * h;
+    }
+  }
+}
+
+// 1/(2m-1) as a compile-time double (the downward-recursion divisor).
+template <int M>
+__device__ __forceinline__ constexpr double inv_odd() {
+  return 1.0 / double(2 * M - 1);
+}
+
+// The order actually evaluated for a requested n_max on the double path:
+// computing F_{n+1} and recursing down buys a few bits at m = n (Sec. 3);
+// it is used from n_max = 9 on, where the paper's F_n alone is above 2e-14.
+__host__ __device__ constexpr int f64_top_order(int n_max) { return n_max >= 9 ? n_max + 1 : n_max; }
+
+// Persistent-grid size for a kernel: resident blocks per SM times SM count.
+template <typename Kernel>
+inline int persistent_grid(Kernel k, int block, size_t smem, int64_t tiles) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t g = (int64_t)sms * per_sm;
+  if (tiles < g) g = tiles;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// Copy a staged tile of `total` contiguous values from shared to global memory
+// with 16-byte vector stores when the destination allows it (streaming stores:
+// the output is written once and not re-read by this kernel).
+template <typename T, int BLOCK>
+__device__ __forceinline__ void store_tile(T *__restrict__ dst, const T *__restrict__ src, int total) {
+  constexpr int V = 16 / sizeof(T);
+  const uintptr_t a = reinterpret_cast<uintptr_t>(dst);
+  if ((a & 15) == 0) {
+    const int nv = total / V;
+    using Vec = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+    const Vec *s = reinterpret_cast<const Vec *>(src);
+    Vec *d = reinterpret_cast<Vec *>(dst);
+    for (int j = threadIdx.x; j < nv; j += BLOCK) __stcs(d + j, s[j]);
+    for (int j = nv * V + threadIdx.x; j < total; j += BLOCK) __stcs(dst + j, src[j]);
+  } else {
+    for (int j = threadIdx.x; j < total; j += BLOCK) __stcs(dst + j, src[j]);
+  }
+}
+
+}  // namespace boys

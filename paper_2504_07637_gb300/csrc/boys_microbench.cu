@@ -1,0 +1,73 @@
+// Throughput microbenchmarks for the ALU roofline of the Boys kernels: how
+// many FP64 / FP32 operations of each kind the GPU retires per second.  Each
+// thread runs 8 independent dependency chains so the pipes, not latency,
+// set the rate.
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/boys_microbench.h"
+#include "boys_common.cuh"
+
+namespace {
+
+constexpr int kChains = 8;
+
+template <int OP>
+__global__ void __launch_bounds__(256) micro_kernel(int64_t iters, double *sink) {
+  double a[kChains];
+  float f[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) {
+    a[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+    f[c] = 1.0f + 1e-3f * (threadIdx.x + c);
+  }
+  const double ka = 0.9999999, kb = 1e-7;
+  const float fa = 0.9999f, fb = 1e-4f;
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+      if constexpr (OP == BOYS_MICRO_DFMA) a[c] = fma(a[c], ka, kb);
+      if constexpr (OP == BOYS_MICRO_DEXP) a[c] = exp(-a[c]) + 0.5;
+      if constexpr (OP == BOYS_MICRO_DSQRT) a[c] = sqrt(a[c]) + 0.25;
+      if constexpr (OP == BOYS_MICRO_DRSQRT) a[c] = rsqrt(a[c]) + 0.25;
+      if constexpr (OP == BOYS_MICRO_DDIV) a[c] = 1.5 / a[c] + 0.25;
+      if constexpr (OP == BOYS_MICRO_FFMA) f[c] = fmaf(f[c], fa, fb);
+      if constexpr (OP == BOYS_MICRO_FEXP2) f[c] = exp2f(-f[c]) + 0.5f;
+      if constexpr (OP == BOYS_MICRO_FSQRT) f[c] = sqrtf(f[c]) + 0.25f;
+      if constexpr (OP == BOYS_MICRO_FDIV) f[c] = 1.5f / f[c] + 0.25f;
+      if constexpr (OP == BOYS_MICRO_FRSQRT) f[c] = rsqrtf(f[c]) + 0.25f;
+    }
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) acc += a[c] + (double)f[c];
+  if (acc == 123.456) sink[0] = acc;  // never true; keeps the chains live
+}
+
+template <int OP>
+int launch(int64_t iters, double *sink, int blocks, cudaStream_t s) {
+  micro_kernel<OP><<<blocks, 256, 0, s>>>(iters, sink);
+  return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" int boys_microbench_launch(int op, int64_t iters, double *sink, int blocks, void *stream) {
+  if (iters < 0 || blocks < 1 || !sink) return BOYS_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (op) {
+    case BOYS_MICRO_DFMA: return launch<BOYS_MICRO_DFMA>(iters, sink, blocks, s);
+    case BOYS_MICRO_DEXP: return launch<BOYS_MICRO_DEXP>(iters, sink, blocks, s);
+    case BOYS_MICRO_DSQRT: return launch<BOYS_MICRO_DSQRT>(iters, sink, blocks, s);
+    case BOYS_MICRO_DRSQRT: return launch<BOYS_MICRO_DRSQRT>(iters, sink, blocks, s);
+    case BOYS_MICRO_DDIV: return launch<BOYS_MICRO_DDIV>(iters, sink, blocks, s);
+    case BOYS_MICRO_FFMA: return launch<BOYS_MICRO_FFMA>(iters, sink, blocks, s);
+    case BOYS_MICRO_FEXP2: return launch<BOYS_MICRO_FEXP2>(iters, sink, blocks, s);
+    case BOYS_MICRO_FSQRT: return launch<BOYS_MICRO_FSQRT>(iters, sink, blocks, s);
+    case BOYS_MICRO_FDIV: return launch<BOYS_MICRO_FDIV>(iters, sink, blocks, s);
+    case BOYS_MICRO_FRSQRT: return launch<BOYS_MICRO_FRSQRT>(iters, sink, blocks, s);
+    default: return BOYS_ERR_ARG;
+  }
+}
+
+extern "C" int boys_microbench_ops_per_thread_iter(void) { return kChains; }

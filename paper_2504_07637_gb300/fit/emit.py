@@ -1,0 +1,139 @@
+"""Generate the CUDA coefficient header from the fitted table (offline tool).
+
+Sec. 3 of the paper proposes generating the evaluation code from the
+coefficient dataset with all loops unrolled; this emits, per order n, a
+device function that evaluates Q~_n(x) = q0 + q1 x + q2 x^2 u(x)/v(x) in the
+root-product form of Eqs. "pz"/"qz": the gathered negative-real-part roots as
+one Horner polynomial, then the quadratic factors (x - y)^2 + a, then the
+linear factors (x - y).  Constants (cut-offs z_nb and c_n) are emitted as
+template specialisations usable from device and host code.
+
+Usage:  python -m paper_2504_07637_gb300.fit.emit
+"""
+from __future__ import annotations
+
+import json
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+PKG = os.path.dirname(HERE)
+COEFF_DIR = os.path.join(PKG, "coeffs")
+CSRC = os.path.join(PKG, "csrc")
+
+
+def d(v: str) -> str:
+    """Decimal string -> C double literal (correctly rounded by Python)."""
+    f = float(v)
+    r = repr(f)
+    if "e" not in r and "." not in r and "inf" not in r:
+        r += ".0"
+    return r
+
+
+def poly_lines(name: str, fac: dict, var: str = "x", fma: str = "fma", ty: str = "double", lit=None) -> list[str]:
+    """Statements computing the monic root-product polynomial into `name`."""
+    lit = lit or d
+    poly = fac["poly"]  # low -> high, monic
+    lines = [f"{ty} {name};"]
+    state = {"first": True}
+
+    def mul(expr: str, indent: str = "") -> None:
+        if state["first"]:
+            lines.append(f"{indent}{name} = {expr};")
+            state["first"] = False
+        else:
+            lines.append(f"{indent}{name} = {name} * {expr};")
+
+    if len(poly) > 1:
+        # Horner on the gathered negative-real-part polynomial (leading coefficient 1)
+        lines.append(f"{{ {ty} h = {var} + {lit(poly[-2])};")
+        for c in reversed(poly[:-2]):
+            lines.append(f"  h = {fma}(h, {var}, {lit(c)});")
+        mul("h", "  ")
+        lines.append("}")
+    for y, a in fac["quad"]:
+        lines.append(f"{{ const {ty} t = {var} - {lit(y)};")
+        mul(f"{fma}(t, t, {lit(a)})", "  ")
+        lines.append("}")
+    for y in fac["lin"]:
+        mul(f"({var} - {lit(y)})")
+    if state["first"]:
+        lines.append(f"{name} = 1;")
+    return lines
+
+
+def op_count(fac: dict) -> int:
+    """FP64 operations of one root-product evaluation (for the roofline)."""
+    deg_poly = len(fac["poly"]) - 1
+    ops = max(0, deg_poly - 1) + (1 if deg_poly >= 1 else 0)
+    nfac = (1 if deg_poly >= 1 else 0) + len(fac["quad"]) + len(fac["lin"])
+    ops += 2 * len(fac["quad"]) + len(fac["lin"]) + max(0, nfac - 1)
+    return ops
+
+
+def emit_f64(table: dict) -> str:
+    fits = {r["n"]: r for r in table["fits"]}
+    nmax = max(fits)
+    missing = [n for n in range(nmax + 1) if n not in fits]
+    if missing:
+        raise SystemExit(f"missing fits for n = {missing}")
+    out = [
+        "// Generated by paper_2504_07637_gb300/fit/emit.py from coeffs/boys_fit_b53.json; do not edit.",
+        "// Per order n: the constrained minimax fit of Q_n (Sec. 2, Eqs. pqz/pz/qz) in root-product form,",
+        "// its cut-off z_{n,53} and c_n = Gamma(n+1/2)/2.",
+        "#pragma once",
+        f"#define BOYS_F64_TABLE_MAX_N {nmax}",
+        "",
+        "template <int N> struct BoysF64;",
+        "",
+    ]
+    host_z, host_c, host_eps, ops = [], [], [], []
+    for n in range(nmax + 1):
+        r = fits[n]
+        host_z.append(d(r["z"]))
+        host_c.append(d(r["c"]))
+        host_eps.append(f"{r['eps_bits']:.3f}")
+        ops.append(op_count(r["u"]) + op_count(r["v"]))
+        body = ["    " + ln for ln in poly_lines("u", r["u"])]
+        body += ["    " + ln for ln in poly_lines("v", r["v"])]
+        out += [
+            f"// n = {n}: N = {r['N']}, exact-arithmetic error 2^-{r['eps_bits']:.2f}",
+            f"template <> struct BoysF64<{n}> {{",
+            f"  static constexpr int kOrderN = {r['N']};",
+            f"  static constexpr double kCutoff = {d(r['z'])};",
+            f"  static constexpr double kC = {d(r['c'])};",
+            f"  static constexpr double kQ0 = {d(r['q0'])};",
+            f"  static constexpr double kQ1 = {d(r['q1'])};",
+            f"  static constexpr double kQ2 = {d(r['q2'])};",
+            f"  static constexpr int kRootOps = {ops[-1]};",
+            "  // u(x) and v(x) as root products; returns u and v separately",
+            "  static __device__ __forceinline__ void uv(double x, double &u_out, double &v_out) {",
+            *body,
+            "    u_out = u;",
+            "    v_out = v;",
+            "  }",
+            "};",
+            "",
+        ]
+    out += [
+        f"static const double kBoysF64CutoffHost[{nmax + 1}] = {{" + ", ".join(host_z) + "};",
+        f"static const double kBoysCHost[{nmax + 1}] = {{" + ", ".join(host_c) + "};",
+        f"static const float kBoysF64FitBitsHost[{nmax + 1}] = {{" + ", ".join(e + "f" for e in host_eps) + "};",
+        f"static const int kBoysF64RootOpsHost[{nmax + 1}] = {{" + ", ".join(map(str, ops)) + "};",
+        "",
+    ]
+    return "\n".join(out)
+
+
+def main():
+    with open(os.path.join(COEFF_DIR, "boys_fit_b53.json")) as fh:
+        t53 = json.load(fh)
+    src = emit_f64(t53)
+    path = os.path.join(CSRC, "boys_coeffs_f64.inc")
+    with open(path, "w") as fh:
+        fh.write(src)
+    print(f"wrote {path}")
+
+
+if __name__ == "__main__":
+    main()

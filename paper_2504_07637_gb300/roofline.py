@@ -1,0 +1,62 @@
+"""Algorithmic work per argument of the Boys evaluation, for the roofline.
+
+Counts are of the method (Sec. 2), not of a particular kernel: below the
+cut-off one evaluation of Q~ in root-product form, one division u/v, one
+exponential (shared with the recursion, Eq. "r"), the half-integer powers
+Q^{n+1/2} and D^{-(n+1/2)} as square-and-multiply plus a square root each,
+one reciprocal of D, and two operations per step of the downward recursion;
+above it (Eq. "limf1") one reciprocal square root, one reciprocal of x and two
+operations per order.  "fma" counts every add, multiply or fused multiply-add
+(each one FP64-pipe instruction).  Bytes per argument are the input value plus
+the n_max+1 outputs.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _fits(bits: int) -> dict:
+    with open(os.path.join(_HERE, "coeffs", f"boys_fit_b{bits}.json")) as fh:
+        return {r["n"]: r for r in json.load(fh)["fits"]}
+
+
+def root_product_ops(fac: dict) -> int:
+    """Adds/multiplies of one monic root-product polynomial as generated."""
+    deg_poly = len(fac["poly"]) - 1
+    ops = deg_poly  # Horner on the gathered polynomial (first step is an add)
+    nfac = (1 if deg_poly >= 1 else 0) + len(fac["quad"]) + len(fac["lin"])
+    ops += 2 * len(fac["quad"]) + len(fac["lin"])  # (x-y), fma(t,t,a) / (x-y)
+    ops += max(0, nfac - 1)  # products joining the factors
+    return ops
+
+
+def square_multiply_ops(k: int) -> int:
+    """Multiplications of x^k by repeated squaring."""
+    if k <= 1:
+        return 0
+    return (k.bit_length() - 1) + (bin(k).count("1") - 1)
+
+
+def f64_counts(n_max: int, n_top: int) -> tuple[dict, dict]:
+    """(below-cut-off, above-cut-off) op counts per argument."""
+    rec = _fits(53)[n_top]
+    below = {
+        "fma": root_product_ops(rec["u"]) + root_product_ops(rec["v"])
+        + 4  # q0 + q1 x + q2 x^2 r
+        + 2 * square_multiply_ops(n_top) + 1 + 1 + 1  # Q^n sqrt(Q), times e, plus x
+        + 2  # c (1/D)^n sqrt(1/D)
+        + 1 + 2 * n_top,  # 2x and the recursion
+        "div": 2,
+        "sqrt": 2,
+        "exp": 1,
+        "rsqrt": 0,
+    }
+    above = {"fma": 1 + 2 * n_max, "div": 1, "sqrt": 0, "exp": 0, "rsqrt": 1}
+    return below, above
+
+
+def bytes_per_arg(n_max: int, elem: int = 8) -> int:
+    return elem * (1 + n_max + 1)

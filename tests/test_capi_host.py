@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads and exports every declared symbol; its
+host-side argument checks answer before any CUDA call (no GPU needed)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import shutil
+
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2504_07637_gb300 import _capi
+    from paper_2504_07637_gb300.build import build_library
+
+    build_library()
+    return _capi
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(boys_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(capi):
+    lib = capi.load()
+    declared = _declared()
+    assert declared, "no declarations found"
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(capi.SIGNATURES) == declared
+
+
+def test_host_argument_checks(capi):
+    f = capi.load().boys_eval_f64
+    assert f(8, -1, 8, 8, None) == 2  # count < 0
+    assert f(8, 10, -1, 8, None) == 3  # n_max < 0
+    assert f(8, 10, capi.load().boys_max_n(53) + 1, 8, None) == 3
+    assert f(None, 0, 8, None, None) == 0  # empty is a no-op
+    assert f(None, 5, 8, 8, None) == 1  # null input
+    assert f(8, 5, 8, None, None) == 1  # null output
+    assert f(0x1004, 5, 8, 0x2000, None) == 4  # misaligned double pointer
+    assert f(8, 2**62, 8, 8, None) == 2  # row count overflows int64
+
+
+def test_status_strings(capi):
+    for code in range(9):
+        assert capi.status_string(code)
+    assert capi.status_string(0) == "ok"
+
+
+def test_table_metadata(capi, oracle_mod):
+    lib = capi.load()
+    assert lib.boys_max_n(53) == 36
+    for n in range(0, 38):
+        assert abs(lib.boys_cutoff(n, 53) / oracle_mod.cutoff(n, 53) - 1) < 1e-13
+    assert np.isnan(lib.boys_cutoff(99, 53))
+    assert [lib.boys_top_order_f64(k) for k in (0, 8, 9, 36, 37)] == [0, 8, 10, 37, -1]
