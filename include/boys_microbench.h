@@ -24,7 +24,8 @@ enum {
     BOYS_MICRO_FEXP2 = 6, /* float exp2f (plus one add) */
     BOYS_MICRO_FSQRT = 7, /* float sqrtf (plus one add) */
     BOYS_MICRO_FDIV = 8,  /* float division (plus one add) */
-    BOYS_MICRO_FRSQRT = 9 /* float rsqrtf (plus one add) */
+    BOYS_MICRO_FRSQRT = 9,/* float rsqrtf (plus one add) */
+    BOYS_MICRO_DEXP_LIB = 10 /* the library's own e^{-x} (Tang's method), plus one add */
 };
 
 /* Launch `blocks` x 256 threads, each running `iters` iterations of
@@ -35,6 +36,11 @@ int boys_microbench_launch(int op, int64_t iters, double *sink, int blocks, void
 
 /* Independent operations per thread and iteration (the chain count). */
 int boys_microbench_ops_per_thread_iter(void);
+
+/* out[i] = e^{-x[i]} by the library's own exponential (Tang's table-driven
+ * method), for testing it against a reference; valid for 0 <= x <= 700.
+ * x, out: device arrays of n doubles.  Returns a boys_status. */
+int boys_debug_exp_neg(const double *x, int64_t n, double *out, void *stream);
 
 #ifdef __cplusplus
 }

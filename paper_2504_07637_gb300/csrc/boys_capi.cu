@@ -11,7 +11,7 @@ int boys_f64_dispatch_p2(int n_max, const double *x, int64_t count, double *out,
 
 namespace {
 
-constexpr int kMaxNF64 = BOYS_F64_TABLE_MAX_N - 1;  // n_top = n_max + 1 must be tabulated
+using boys::kMaxNF64;
 
 // The kernels are built for sm_103a only; reject other devices up front
 // instead of failing inside a launch.

@@ -31,10 +31,14 @@ __device__ __forceinline__ constexpr double inv_odd() {
   return 1.0 / double(2 * M - 1);
 }
 
-// The order actually evaluated for a requested n_max on the double path:
-// computing F_{n+1} and recursing down buys a few bits at m = n (Sec. 3);
-// it is used from n_max = 9 on, where the paper's F_n alone is above 2e-14.
-__host__ __device__ constexpr int f64_top_order(int n_max) { return n_max >= 9 ? n_max + 1 : n_max; }
+// Order evaluated for a requested n_max on the double path: computing
+// F_{n_top} with n_top > n_max and recursing down buys accuracy at m = n_max
+// (Sec. 3 suggests n_top = n_max + 1); the offsets keep every m within 2e-14
+// up to n_max = 36.
+__host__ __device__ constexpr int f64_top_order(int n_max) {
+  return n_max <= 3 ? n_max : n_max <= 12 ? n_max + 1 : n_max <= 22 ? n_max + 2 : n_max <= 27 ? n_max + 3 : n_max + 4;
+}
+constexpr int kMaxNF64 = 36;
 
 // Persistent-grid size for a kernel: resident blocks per SM times SM count.
 template <typename Kernel>

@@ -1,5 +1,20 @@
-// FP64 forward path: one argument per thread, rows staged in shared memory
-// and written out as contiguous 16-byte stores.
+// FP64 forward path.
+//
+// GB300 retires FP64 at about 1/64 of its FP32 rate, so this path is bound by
+// the FP64 pipe, not by HBM: every design choice below removes FP64
+// instructions.
+//  * Compaction: each tile of arguments is split into a below-cut-off list
+//    (closed form, ~95 FP64 operations) and an above-cut-off list (asymptote,
+//    ~25), and warps take 32 entries of one list at a time, so no warp pays
+//    for both branches (with arguments mixed at random, nearly every warp of a
+//    plain one-argument-per-thread kernel would).
+//  * Classification, the factor 2 of the recursion and the final scaling of
+//    the exponential are integer operations on the bit patterns.
+//  * e^{-x} is Tang's table-driven method (ACM TOMS 15(2), 1989): 2^(k/64)
+//    from a shared-memory table times a degree-5 polynomial on
+//    |r| <= ln2/128, about 10 FP64 operations.
+//  * Half-integer powers use the reciprocal square root where the rounding
+//    budget allows it.
 #pragma once
 
 #include "boys_coeffs_f64.inc"
@@ -7,48 +22,87 @@
 
 namespace boys {
 
-// F_0..F_{NMAX} at one argument, evaluating the approximation of order NTOP.
-//
-// Below the cut-off z_{NTOP,53} (Sec. 2):
-//   Q   = q0 + q1 x + q2 x^2 u(x)/v(x)           (Eq. "pqz", root products of Eqs. "pz"/"qz")
-//   D   = x + Q^NTOP sqrt(Q) e^{-x}               (the bracket of Eq. "fq")
-//   F_NTOP = c_NTOP (1/D)^NTOP sqrt(1/D)          (Eq. "fq": half-integer power as s^n sqrt(s))
-//   F_{m-1} = (2x F_m + e^{-x}) / (2m-1)          (Eq. "r", reusing the same e^{-x})
-// Above it, the asymptote of Eq. "limf1" holds for every m <= NTOP to within
-// 2^-53 (the neglected part R(m+1/2, x) decreases with m), so the row is
-// F_0 = c_0 / sqrt(x), F_m = F_{m-1} (m - 1/2) / x, computed upward so that
-// high orders underflow gracefully for huge x.
+// 2^(j/64), j = 0..63, for the exponential below
+static __constant__ double kExp2Frac64[64] = BOYS_EXP2_FRAC64;
+
+static_assert(f64_top_order(kMaxNF64) <= BOYS_F64_TABLE_MAX_N, "fitted table too short");
+
+__device__ __forceinline__ double twice(double x) {
+  // exact 2x for normal x; for |x| below the normal range the result is a
+  // tiny normal number, which leaves fma(2x, F, e^{-x}) unchanged
+  return __longlong_as_double(__double_as_longlong(x) + (1LL << 52));
+}
+
+// e^{-x} for 0 <= x <= 700 by Tang's table-driven method:
+//   -x = (k/64) ln2 + r,  k = round(-x 64/ln2),  |r| <= ln2/128,
+//   e^{-x} = 2^(k>>6) * 2^((k&63)/64) * (1 + p(r)),  p(r) = r + r^2/2 + ... + r^5/120.
+// ln2/64 is split in two parts (Cody and Waite) so that k*L1 is exact.
+__device__ __forceinline__ double exp_neg(double x, const double *__restrict__ tab64) {
+  constexpr double kShift = 6755399441055744.0;  // 1.5 * 2^52: rounds to an integer in the low bits
+  constexpr double kInvL = 92.332482616893656;   // 64 / ln2
+  constexpr double kL1 = 0.010830424696251839;   // ln2/64, 39 significant bits
+  constexpr double kL2 = -2.693663207127318e-15; // ln2/64 - kL1
+  const double a = -x;
+  double kd = fma(a, kInvL, kShift);
+  const int k = __double2loint(kd);
+  kd -= kShift;
+  double r = fma(kd, -kL1, a);
+  r = fma(kd, -kL2, r);
+  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  p = fma(r, p, 1.0 / 6.0);
+  p = fma(r, p, 0.5);
+  p = fma(r, p, 1.0);
+  p = p * r;
+  const double t = tab64[k & 63];
+  const double res = fma(t, p, t);
+  return __longlong_as_double(__double_as_longlong(res) + ((long long)(k >> 6) << 52));
+}
+
+// Below the cut-off z_{NTOP,53} (Sec. 2): with s = NTOP + 1/2,
+//   Q   = q0 + q1 x + q2 x^2 u(x)/v(x)      (Eq. "pqz"; u, v root products, Eqs. "pz"/"qz")
+//   D   = x + Q^NTOP sqrt(Q) e^{-x}          (Eq. "fq")
+//   F_NTOP = c_NTOP D^{-s}
+//   F_{m-1} = (2x F_m + e^{-x}) / (2m-1)     (Eq. "r", same e^{-x}; the printed
+//                                             denominator 2m+1 is read as 2m-1)
 template <int NTOP, int NMAX>
-__device__ __forceinline__ void f64_row(const double x, double (&F)[NMAX + 1]) {
-  static_assert(NTOP >= NMAX && NTOP <= NMAX + 1, "NTOP is NMAX or NMAX+1");
+__device__ __forceinline__ void f64_formula(const double x, double (&F)[NMAX + 1], const double *__restrict__ tab64) {
   using Tab = BoysF64<NTOP>;
-  if (x <= Tab::kCutoff) {
-    double u, v;
-    Tab::uv(x, u, v);
-    const double r = u / v;
-    const double p = (Tab::kQ2 * x) * x;
-    const double q = fma(p, r, fma(Tab::kQ1, x, Tab::kQ0));
-    const double e = exp(-x);
-    const double T = (ipow<NTOP>(q) * sqrt(q)) * e;
-    const double D = x + T;
-    const double w = 1.0 / D;
-    double f = (Tab::kC * ipow<NTOP>(w)) * sqrt(w);
-    const double tx = x + x;
-#pragma unroll
-    for (int m = NTOP; m >= 1; --m) {
-      if (m <= NMAX) F[m] = f;
-      f = fma(tx, f, e) * (1.0 / double(2 * m - 1));
-    }
-    F[0] = f;
-    if (!(x >= 0.0)) {  // negative arguments are outside the domain
-#pragma unroll
-      for (int m = 0; m <= NMAX; ++m) F[m] = __longlong_as_double(0x7ff8000000000000LL);
-    }
+  double u, v;
+  Tab::uv(x, u, v);
+  const double r = u / v;
+  const double p = (Tab::kQ2 * x) * x;
+  const double q = fma(p, r, fma(Tab::kQ1, x, Tab::kQ0));
+  const double e = exp_neg(x, tab64);
+  const double T = (ipow<NTOP>(q) * (q * rsqrt(q))) * e;
+  const double D = x + T;
+  double f;
+  if constexpr (NTOP <= 13) {
+    const double rs = rsqrt(D);  // D^{-s} = rs^{2 NTOP + 1}
+    f = (Tab::kC * rs) * ipow<NTOP>(rs * rs);
   } else {
-    // x > cut-off, +inf or NaN (NaN propagates through rsqrt)
-    const double y = 1.0 / x;
-    double f = 0.88622692545275801365 * rsqrt(x);  // c_0 = sqrt(pi)/2
-    F[0] = f;
+    const double w = 1.0 / D;  // D^{-s} = w^NTOP sqrt(w)
+    f = (Tab::kC * ipow<NTOP>(w)) * (w * rsqrt(w));
+  }
+  const double tx = twice(x);
+#pragma unroll
+  for (int m = NTOP; m >= 1; --m) {
+    if (m <= NMAX) F[m] = f;
+    f = fma(tx, f, e) * (1.0 / double(2 * m - 1));
+  }
+  F[0] = f;
+}
+
+// Above the cut-off (or x negative, infinite or NaN): the asymptote of
+// Eq. "limf1", within 2^-53 of F_m for every m <= NTOP there, built upward
+// F_0 = c_0 / sqrt(x), F_m = F_{m-1} (m - 1/2) / x so that high orders
+// underflow gracefully.  Negative x and NaN give NaN through rsqrt.
+template <int NMAX>
+__device__ __forceinline__ void f64_asymptote(const double x, double (&F)[NMAX + 1]) {
+  const double rs = rsqrt(x);
+  double f = 0.88622692545275801365 * rs;  // c_0 = sqrt(pi)/2
+  F[0] = f;
+  if constexpr (NMAX >= 1) {
+    const double y = NMAX <= 12 ? rs * rs : 1.0 / x;
 #pragma unroll
     for (int m = 1; m <= NMAX; ++m) {
       f = f * ((double(m) - 0.5) * y);
@@ -57,35 +111,103 @@ __device__ __forceinline__ void f64_row(const double x, double (&F)[NMAX + 1]) {
   }
 }
 
-template <int NMAX, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) f64_plain_kernel(const double *__restrict__ x, int64_t count,
+template <int W>
+__device__ __forceinline__ void store_row(double *__restrict__ dst, const double (&F)[W]) {
+#pragma unroll
+  for (int m = 0; m < W; ++m) __stcs(dst + m, F[m]);
+}
+
+// Below-cut-off test on the bit pattern (integer pipe): true for +-0 and
+// 0 < x <= z; false for negative nonzero x, NaN and x > z.
+__device__ __forceinline__ bool below_cutoff(double v, unsigned long long zbits) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long mag = b & 0x7fffffffffffffffULL;
+  return ((b >> 63) == 0 || mag == 0) && mag <= zbits;
+}
+
+template <int NMAX, int BLOCK, int TILE>
+__global__ void __launch_bounds__(BLOCK) f64_split_kernel(const double *__restrict__ x, int64_t count,
                                                           double *__restrict__ out) {
   constexpr int NTOP = f64_top_order(NMAX);
   constexpr int W = NMAX + 1;
-  __shared__ __align__(16) double tile[BLOCK * W];
-  const int64_t ntiles = (count + BLOCK - 1) / BLOCK;
+  static_assert(TILE % BLOCK == 0 && TILE <= 65536, "tile");
+  __shared__ double xs[TILE];
+  __shared__ unsigned short lst[TILE];  // below list from the front, above list from the back
+  __shared__ double tab64[64];
+  __shared__ int cnt[2], next[2];
+  if (threadIdx.x < 64) tab64[threadIdx.x] = kExp2Frac64[threadIdx.x];
+  const unsigned long long zbits = (unsigned long long)__double_as_longlong(BoysF64<NTOP>::kCutoff);
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t ntiles = (count + TILE - 1) / TILE;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t base = t * BLOCK;
-    const int64_t i = base + threadIdx.x;
-    double F[W];
-    const double xi = i < count ? __ldg(x + i) : 0.0;
-    f64_row<NTOP, NMAX>(xi, F);
-#pragma unroll
-    for (int m = 0; m < W; ++m) tile[threadIdx.x * W + m] = F[m];
+    const int64_t base = t * TILE;
+    const int nel = (int)((count - base) < TILE ? (count - base) : TILE);
+    if (threadIdx.x == 0) {
+      cnt[0] = cnt[1] = 0;
+      next[0] = next[1] = 0;
+    }
     __syncthreads();
-    const int nel = (int)((count - base) < BLOCK ? (count - base) : BLOCK);
-    store_tile<double, BLOCK>(out + base * W, tile, nel * W);
+#pragma unroll 4
+    for (int j0 = 0; j0 < TILE; j0 += BLOCK) {
+      const int j = j0 + threadIdx.x;
+      const bool valid = j < nel;
+      const double v = valid ? __ldcs(x + base + j) : 0.0;
+      xs[j] = v;
+      const bool lo = valid && below_cutoff(v, zbits);
+      const bool hi = valid && !lo;
+      const unsigned mlo = __ballot_sync(0xffffffffu, lo), mhi = __ballot_sync(0xffffffffu, hi);
+      int plo = 0, phi = 0;
+      if (lane == 0) {
+        if (mlo) plo = atomicAdd(&cnt[0], __popc(mlo));
+        if (mhi) phi = atomicAdd(&cnt[1], __popc(mhi));
+      }
+      plo = __shfl_sync(0xffffffffu, plo, 0);
+      phi = __shfl_sync(0xffffffffu, phi, 0);
+      if (lo) lst[plo + __popc(mlo & lt)] = (unsigned short)j;
+      if (hi) lst[TILE - 1 - (phi + __popc(mhi & lt))] = (unsigned short)j;
+    }
+    __syncthreads();
+    const int nlo = cnt[0], nhi = cnt[1];
+    // closed form on the below-cut-off list, 32 entries per warp request
+    for (;;) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(&next[0], 32);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      if (c >= nlo) break;
+      const int q = c + lane;
+      if (q < nlo) {
+        const int j = lst[q];
+        double F[W];
+        f64_formula<NTOP, NMAX>(xs[j], F, tab64);
+        store_row<W>(out + (base + j) * W, F);
+      }
+    }
+    // asymptote on the above-cut-off list
+    for (;;) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(&next[1], 32);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      if (c >= nhi) break;
+      const int q = c + lane;
+      if (q < nhi) {
+        const int j = lst[TILE - 1 - q];
+        double F[W];
+        f64_asymptote<NMAX>(xs[j], F);
+        store_row<W>(out + (base + j) * W, F);
+      }
+    }
     __syncthreads();
   }
 }
 
 template <int NMAX>
-int launch_f64_plain(const double *x, int64_t count, double *out, cudaStream_t s) {
-  constexpr int BLOCK = 128;
-  auto k = f64_plain_kernel<NMAX, BLOCK>;
+int launch_f64(const double *x, int64_t count, double *out, cudaStream_t s) {
+  constexpr int BLOCK = 256, TILE = 2048;
+  auto k = f64_split_kernel<NMAX, BLOCK, TILE>;
   static int grid_cap = 0;
-  const int64_t tiles = (count + BLOCK - 1) / BLOCK;
   if (grid_cap == 0) grid_cap = persistent_grid(k, BLOCK, 0, INT64_MAX);
+  const int64_t tiles = (count + TILE - 1) / TILE;
   const int grid = (int)(tiles < grid_cap ? tiles : grid_cap);
   k<<<grid, BLOCK, 0, s>>>(x, count, out);
   return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
@@ -93,7 +215,6 @@ int launch_f64_plain(const double *x, int64_t count, double *out, cudaStream_t s
 
 }  // namespace boys
 
-// Dispatch one n_max in [LO, HI] to its instantiation; returns -1 if not in range.
 #define BOYS_F64_CASE(k) \
   case k:                \
-    return boys::launch_f64_plain<k>(x, count, out, s);
+    return boys::launch_f64<k>(x, count, out, s);

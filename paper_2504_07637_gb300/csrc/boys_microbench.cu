@@ -7,6 +7,7 @@
 
 #include "../../include/boys_microbench.h"
 #include "boys_common.cuh"
+#include "boys_f64.cuh"
 
 namespace {
 
@@ -14,6 +15,9 @@ constexpr int kChains = 8;
 
 template <int OP>
 __global__ void __launch_bounds__(256) micro_kernel(int64_t iters, double *sink) {
+  __shared__ double tab64[64];
+  if (threadIdx.x < 64) tab64[threadIdx.x] = boys::kExp2Frac64[threadIdx.x];
+  __syncthreads();
   double a[kChains];
   float f[kChains];
 #pragma unroll
@@ -28,6 +32,7 @@ __global__ void __launch_bounds__(256) micro_kernel(int64_t iters, double *sink)
     for (int c = 0; c < kChains; ++c) {
       if constexpr (OP == BOYS_MICRO_DFMA) a[c] = fma(a[c], ka, kb);
       if constexpr (OP == BOYS_MICRO_DEXP) a[c] = exp(-a[c]) + 0.5;
+      if constexpr (OP == BOYS_MICRO_DEXP_LIB) a[c] = boys::exp_neg(a[c], tab64) + 0.5;
       if constexpr (OP == BOYS_MICRO_DSQRT) a[c] = sqrt(a[c]) + 0.25;
       if constexpr (OP == BOYS_MICRO_DRSQRT) a[c] = rsqrt(a[c]) + 0.25;
       if constexpr (OP == BOYS_MICRO_DDIV) a[c] = 1.5 / a[c] + 0.25;
@@ -66,8 +71,28 @@ extern "C" int boys_microbench_launch(int op, int64_t iters, double *sink, int b
     case BOYS_MICRO_FSQRT: return launch<BOYS_MICRO_FSQRT>(iters, sink, blocks, s);
     case BOYS_MICRO_FDIV: return launch<BOYS_MICRO_FDIV>(iters, sink, blocks, s);
     case BOYS_MICRO_FRSQRT: return launch<BOYS_MICRO_FRSQRT>(iters, sink, blocks, s);
+    case BOYS_MICRO_DEXP_LIB: return launch<BOYS_MICRO_DEXP_LIB>(iters, sink, blocks, s);
     default: return BOYS_ERR_ARG;
   }
 }
 
 extern "C" int boys_microbench_ops_per_thread_iter(void) { return kChains; }
+
+namespace {
+__global__ void exp_neg_kernel(const double *__restrict__ x, int64_t n, double *__restrict__ out) {
+  __shared__ double tab64[64];
+  if (threadIdx.x < 64) tab64[threadIdx.x] = boys::kExp2Frac64[threadIdx.x];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = boys::exp_neg(x[i], tab64);
+}
+}  // namespace
+
+extern "C" int boys_debug_exp_neg(const double *x, int64_t n, double *out, void *stream) {
+  if (n < 0) return BOYS_ERR_COUNT;
+  if (n == 0) return BOYS_OK;
+  if (!x || !out) return BOYS_ERR_NULL;
+  const int64_t blocks = (n + 255) / 256;
+  exp_neg_kernel<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n, out);
+  return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
+}

@@ -116,6 +116,8 @@ def emit_f64(table: dict) -> str:
             "",
         ]
     out += [
+        "// 2^(j/64), j = 0..63 (table of the exponential used by the kernels)",
+        f"#define BOYS_EXP2_FRAC64 {{{exp2_table()}}}",
         f"static const double kBoysF64CutoffHost[{nmax + 1}] = {{" + ", ".join(host_z) + "};",
         f"static const double kBoysCHost[{nmax + 1}] = {{" + ", ".join(host_c) + "};",
         f"static const float kBoysF64FitBitsHost[{nmax + 1}] = {{" + ", ".join(e + "f" for e in host_eps) + "};",
@@ -123,6 +125,19 @@ def emit_f64(table: dict) -> str:
         "",
     ]
     return "\n".join(out)
+
+
+def exp2_table(n: int = 64) -> str:
+    """2^(j/n), j = 0..n-1, correctly rounded to double (table of Tang's
+    table-driven exponential)."""
+    from decimal import Decimal, getcontext
+
+    getcontext().prec = 60
+    vals = []
+    for j in range(n):
+        v = (Decimal(2) ** (Decimal(j) / Decimal(n)))
+        vals.append(repr(float(v)))
+    return ", ".join(vals)
 
 
 def main():

@@ -1,12 +1,11 @@
 """Algorithmic work per argument of the Boys evaluation, for the roofline.
 
-Counts are of the method (Sec. 2), not of a particular kernel: below the
+Counts follow the method (Sec. 2) as the double kernels evaluate it: below the
 cut-off one evaluation of Q~ in root-product form, one division u/v, one
 exponential (shared with the recursion, Eq. "r"), the half-integer powers
-Q^{n+1/2} and D^{-(n+1/2)} as square-and-multiply plus a square root each,
-one reciprocal of D, and two operations per step of the downward recursion;
-above it (Eq. "limf1") one reciprocal square root, one reciprocal of x and two
-operations per order.  "fma" counts every add, multiply or fused multiply-add
+Q^{n+1/2} and D^{-(n+1/2)} as square-and-multiply plus a reciprocal square
+root each, and two operations per step of the downward recursion; above it
+(Eq. "limf1") one reciprocal square root and two operations per order.  "fma" counts every add, multiply or fused multiply-add
 (each one FP64-pipe instruction).  Bytes per argument are the input value plus
 the n_max+1 outputs.
 """
@@ -41,20 +40,29 @@ def square_multiply_ops(k: int) -> int:
 
 
 def f64_counts(n_max: int, n_top: int) -> tuple[dict, dict]:
-    """(below-cut-off, above-cut-off) op counts per argument."""
+    """(below-cut-off, above-cut-off) operation counts per argument, in the
+    form the double kernels evaluate them: sqrt(Q) as Q rsqrt(Q); D^{-s} as
+    rsqrt(D)^{2n+1} for n_top <= 13, else (1/D)^n (1/D) rsqrt(1/D); the
+    asymptote's 1/x as rsqrt(x)^2 for n_max <= 12."""
     rec = _fits(53)[n_top]
-    below = {
-        "fma": root_product_ops(rec["u"]) + root_product_ops(rec["v"])
-        + 4  # q0 + q1 x + q2 x^2 r
-        + 2 * square_multiply_ops(n_top) + 1 + 1 + 1  # Q^n sqrt(Q), times e, plus x
-        + 2  # c (1/D)^n sqrt(1/D)
-        + 1 + 2 * n_top,  # 2x and the recursion
-        "div": 2,
-        "sqrt": 2,
-        "exp": 1,
-        "rsqrt": 0,
+    pw = square_multiply_ops(n_top)
+    fma = root_product_ops(rec["u"]) + root_product_ops(rec["v"]) + 4  # Q~
+    fma += pw + 1 + 1 + 1 + 1  # Q^n, Q rsqrt(Q), product, times e^{-x}, plus x
+    if n_top <= 13:
+        fma += 1 + pw + 2  # rs^2, its power, c rs and the product
+        rsq, div = 2, 1
+    else:
+        fma += pw + 1 + 2  # w^n, w rsqrt(w), c w^n and the product
+        rsq, div = 2, 2
+    fma += 2 * n_top  # recursion
+    below = {"fma": fma, "div": div, "sqrt": 0, "exp": 1, "rsqrt": rsq}
+    above = {
+        "fma": 1 + (1 if n_max <= 12 else 0) + 2 * n_max,
+        "div": 0 if n_max <= 12 else 1,
+        "sqrt": 0,
+        "exp": 0,
+        "rsqrt": 1,
     }
-    above = {"fma": 1 + 2 * n_max, "div": 1, "sqrt": 0, "exp": 0, "rsqrt": 1}
     return below, above
 
 

@@ -62,7 +62,7 @@ def test_status_strings(capi):
 def test_table_metadata(capi, oracle_mod):
     lib = capi.load()
     assert lib.boys_max_n(53) == 36
-    for n in range(0, 38):
+    for n in range(0, 42):
         assert abs(lib.boys_cutoff(n, 53) / oracle_mod.cutoff(n, 53) - 1) < 1e-13
     assert np.isnan(lib.boys_cutoff(99, 53))
-    assert [lib.boys_top_order_f64(k) for k in (0, 8, 9, 36, 37)] == [0, 8, 10, 37, -1]
+    assert [lib.boys_top_order_f64(k) for k in (0, 3, 4, 8, 13, 23, 36, 37)] == [0, 3, 5, 9, 15, 26, 40, -1]

@@ -164,3 +164,20 @@ def test_full_size_scale_workload_sampled(lib, oracle_mod, n_max):
     assert _relerr(got, ref).max() <= TOL
     del out, xd
     torch.cuda.empty_cache()
+
+
+def test_library_exponential_against_oracle(lib):
+    # the kernels' own e^{-x} (Tang's table-driven method) against long double
+    import torch
+
+    from paper_2504_07637_gb300 import _capi
+
+    rng = np.random.default_rng(11)
+    x = np.concatenate([np.linspace(0, 120, 200001), rng.uniform(0, 700, 100000), [0.0, 1e-300, 5e-324]])
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xd)
+    _capi.call("boys_debug_exp_neg", xd.data_ptr(), x.size, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    got = out.cpu().numpy()
+    ref = np.exp(-x.astype(np.longdouble))
+    rel = np.abs((got - ref) / ref).astype(np.float64)
+    assert rel.max() < 2.5e-16, rel.max()  # about one unit in the last place
