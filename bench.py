@@ -31,8 +31,12 @@ WORKLOADS = {
     "scale_f64_n0": dict(count=1 << 26, n_max=0, dtype="f64"),
     "scale_f64_n4": dict(count=1 << 26, n_max=4, dtype="f64"),
     "scale_f64_n16": dict(count=1 << 26, n_max=16, dtype="f64"),
-    # small case of the same kernel for detailed profiling (output still larger than L2)
+    # the float path on the same arguments rounded to float
+    "scale_f32_n8": dict(count=1 << 26, n_max=8, dtype="f32"),
+    "scale_f32_n16": dict(count=1 << 26, n_max=16, dtype="f32"),
+    # small cases of the same kernels for detailed profiling (outputs still larger than L2)
     "scale_f64_n8_small": dict(count=1 << 22, n_max=8, dtype="f64"),
+    "scale_f32_n8_small": dict(count=1 << 24, n_max=8, dtype="f32"),
 }
 METRIC = "G F_m values/s at stated max rel err (FP64, FP32); % of ALU/HBM roofline"
 TOL = {"f64": 2e-14, "f32": 2e-6}
@@ -266,6 +270,16 @@ def traffic_record(kernel_key: str):
     return rec.get("bytes_per_launch") if h.hexdigest() == rec.get("sha256") else None
 
 
+def measured_peaks():
+    """Measured HBM bandwidth if present, else the earlier GB300 figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
@@ -285,14 +299,17 @@ def main():
     device = torch.device("cuda", local)
     _capi.load()
     n_max, count = wl["n_max"], wl["count"]
-    x_host = workloads.scale(count, seed=workloads.SEED_BASE + 1 + rank)
+    f32 = wl["dtype"] == "f32"
+    np_t, th_t, esz = (np.float32, torch.float32, 4) if f32 else (np.float64, torch.float64, 8)
+    fn = "boys_eval_f32" if f32 else "boys_eval_f64"
+    x_host = workloads.scale(count, seed=workloads.SEED_BASE + 1 + rank).astype(np_t)
     x = torch.from_numpy(x_host).to(device)
-    out = torch.empty((count, n_max + 1), dtype=torch.float64, device=device)
+    out = torch.empty((count, n_max + 1), dtype=th_t, device=device)
     stream = torch.cuda.current_stream(device)
     sptr = stream.cuda_stream
 
     def step():
-        _capi.call("boys_eval_f64", x.data_ptr(), count, n_max, out.data_ptr(), sptr)
+        _capi.call(fn, x.data_ptr(), count, n_max, out.data_ptr(), sptr)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -322,7 +339,10 @@ def main():
     launches = args.steps  # one kernel per evaluation call
 
     extras = {}
-    if not args.no_extras:
+    hbm_peak, hbm_src = measured_peaks()
+    hbm_bytes = roofline.bytes_per_arg(n_max, esz) * count
+    hbm_gbs = hbm_bytes / (ms / 1e3) / 1e9
+    if not args.no_extras and not f32:
         # ALU roofline from live microbenchmarks of the FP64 operations
         rates = microbench(_capi, device)
         n_top = _capi.load().boys_top_order_f64(n_max)
@@ -335,8 +355,7 @@ def main():
         fma_equiv = t_arg * rates["fma"]  # FP64-pipe instruction equivalents per argument
         achieved = fma_equiv * count / (ms / 1e3) / 1e12
         peak = rates["fma"] / 1e12
-        hbm_bytes = roofline.bytes_per_arg(n_max) * count
-        traffic = traffic_record(f"f64_plain_kernel<{n_max}>/scale_2^26")
+        traffic = traffic_record(f"f64_split_kernel<{n_max}>/scale_2^26")
         extras["roofline"] = {
             "bound": "alu",
             "achieved": round(achieved, 5),
@@ -345,35 +364,37 @@ def main():
             "frac": round(achieved / peak, 4),
             "traffic": traffic,
             "note": "FP64-pipe instruction equivalents per second (1 per add/mul/fma; exp, sqrt, rsqrt and div "
-            "weighted by their measured cost) vs the measured DFMA rate; "
+            "weighted by their measured cost) vs the DFMA rate measured in this run; "
             f"{frac_below:.3f} of arguments below z_{{{n_top},53}}",
-            "hbm": {
-                "achieved_gbs": round(hbm_bytes / (ms / 1e3) / 1e9, 1),
-                "peak_gbs": 6777.0,
-                "frac": round(hbm_bytes / (ms / 1e3) / 1e9 / 6777.0, 4),
-            },
+            "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 4),
+                    "peak_source": hbm_src},
             "measured_rates_gops": {k: round(v / 1e9, 2) for k, v in rates.items()},
         }
-        # end to end through the C ABI with host buffers: pinned host memory is
-        # read and written in place by the kernel over the CPU-GPU link
+    elif not args.no_extras:
+        n_top = _capi.load().boys_top_order_f32(n_max)
+        z = _capi.load().boys_cutoff(n_top, 24)
+        extras["roofline"] = {
+            "bound": "hbm",
+            "achieved": round(hbm_gbs, 1),
+            "peak": hbm_peak,
+            "unit": "GB/s",
+            "frac": round(hbm_gbs / hbm_peak, 4),
+            "traffic": traffic_record(f"f32_split_kernel<{n_max}>/scale_2^26"),
+            "note": f"{roofline.bytes_per_arg(n_max, esz)} algorithmic bytes per argument (x in, n_max+1 floats out) "
+            f"vs the {hbm_src} copy bandwidth; {float(np.mean(x_host <= z)):.3f} of arguments below z_{{{n_top},24}}",
+        }
+    if not args.no_extras:
+        # end to end through the C ABI with host buffers: pinned host arrays are
+        # streamed through a device workspace in chunks whose copies overlap
+        # the neighbouring chunk's kernel (boys_eval_f64_host)
         xp = torch.from_numpy(x_host).pin_memory()
-        op = torch.empty((count, n_max + 1), dtype=torch.float64, pin_memory=True)
-
-        how = "boys_eval_f64 on pinned host buffers (zero-copy over the CPU-GPU link), host wall clock"
+        op = torch.empty((count, n_max + 1), dtype=th_t, pin_memory=True)
+        ws_bytes = 1 << 30
+        wsp = torch.empty(ws_bytes, dtype=torch.uint8, device=device)
+        how = f"{fn}_host: pinned host in/out, 1 GiB device workspace, chunked copies overlapped with compute; host wall clock"
 
         def e2e_step():
-            _capi.call("boys_eval_f64", xp.data_ptr(), count, n_max, op.data_ptr(), sptr)
-
-        try:
-            e2e_step()
-        except _capi.BoysError:
-            # host memory not mapped in place: copy in, evaluate, copy out
-            how = "pinned host -> device copy, boys_eval_f64, device -> pinned host copy; host wall clock"
-
-            def e2e_step():
-                x.copy_(xp, non_blocking=True)
-                _capi.call("boys_eval_f64", x.data_ptr(), count, n_max, out.data_ptr(), sptr)
-                op.copy_(out, non_blocking=True)
+            _capi.call(fn + "_host", xp.data_ptr(), count, n_max, op.data_ptr(), wsp.data_ptr(), ws_bytes, sptr)
 
         e2e_step()
         torch.cuda.synchronize()
@@ -386,13 +407,13 @@ def main():
         extras["e2e"] = {
             "value": round(count * (n_max + 1) * ws / dt / 1e9, 4),
             "unit": "G F_m values/s",
-            "h2d_bytes_per_step": 8 * count,
-            "d2h_bytes_per_step": 8 * count * (n_max + 1),
+            "h2d_bytes_per_step": esz * count,
+            "d2h_bytes_per_step": esz * count * (n_max + 1),
             "how": how,
         }
-        del xp, op
+        del xp, op, wsp
     if rank == 0 and not args.no_cpu_baseline:
-        extras["cpu_baseline"] = oracle_rate(x_host, n_max)
+        extras["cpu_baseline"] = oracle_rate(x_host.astype(np.float64), n_max)
 
     if rank == 0:
         line = {
@@ -409,7 +430,7 @@ def main():
             "dtype": wl["dtype"],
             "data": "synthetic",
             "config": {
-                "workload": f"{args.workload}: 2^26 arguments x = p R^2 per GPU, n_max={n_max}",
+                "workload": f"{args.workload}: {count} arguments x = p R^2 per GPU ({wl['dtype']}), n_max={n_max}",
                 "global_batch": count * ws,
                 "n_max": n_max,
                 "max_rel_err": TOL[wl["dtype"]],

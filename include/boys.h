@@ -73,6 +73,49 @@ int boys_top_order_f64(int n_max);
  * Max relative error against the exact F_m: 2e-14 for every m. */
 boys_status boys_eval_f64(const double *x, int64_t count, int n_max, double *out, void *stream);
 
+/* The order n_top whose approximation the float path evaluates for n_max
+ * (n_max itself up to 8, n_max + 1 above); -1 if unsupported. */
+int boys_top_order_f32(int n_max);
+
+/* FP32 forward: the same method in single precision, with float coefficients
+ * from fits one order above the paper's single-precision column and the
+ * error-amplifying steps (q0 + q1 x, Q^{n+1/2}, e^{-x}, D, D^{-(n+1/2)}) in
+ * float-float arithmetic (Sec. 3 suggests extra precision for full 24-bit
+ * results).
+ *   x:   device, [count] floats
+ *   out: device, [count, n_max+1] floats, row-major
+ * Max relative error against the exact F_m at the float argument: 2e-6 for
+ * every m where F_m >= FLT_MIN; below FLT_MIN (subnormal results) the error
+ * is within 2e-6 relative plus one subnormal unit. */
+boys_status boys_eval_f32(const float *x, int64_t count, int n_max, float *out, void *stream);
+
+/* Device workspace, in bytes, that boys_eval_f64_host needs to stream chunks
+ * of `chunk` arguments (rounded up to 2048) with double buffering; 0 for
+ * invalid arguments. */
+size_t boys_eval_f64_host_workspace(int n_max, int64_t chunk);
+
+/* FP64 forward from and to HOST memory (the same results as boys_eval_f64).
+ *   x_host:    host (or device), [count] doubles
+ *   out_host:  host (or device), [count, n_max+1] doubles, row-major
+ *   workspace: device memory, 256-byte aligned, ws_bytes long; the arguments
+ *              are processed in chunks of ws_bytes / (16 (n_max+2)) (at least
+ *              2048, else BOYS_ERR_WORKSPACE), each copied in, evaluated and
+ *              copied out; the copies of one chunk run on the copy engines
+ *              while the neighbouring chunk is evaluated.
+ * Page-locked (pinned) host memory is needed for the copies to overlap; with
+ * pageable memory the driver copies synchronously.  The library keeps one
+ * helper stream and two events per device (created on the first call) to
+ * overlap the chunks; work on `stream` that follows the call waits for all of
+ * it.  Asynchronous: synchronise `stream` before reading out_host. */
+boys_status boys_eval_f64_host(const double *x_host, int64_t count, int n_max, double *out_host, void *workspace,
+                               size_t ws_bytes, void *stream);
+
+/* Workspace size and host-buffer entry point of the float path; the same
+ * contract as the double versions above, with float arrays. */
+size_t boys_eval_f32_host_workspace(int n_max, int64_t chunk);
+boys_status boys_eval_f32_host(const float *x_host, int64_t count, int n_max, float *out_host, void *workspace,
+                               size_t ws_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,12 @@ SIGNATURES = {
     "boys_cutoff": (c_double, [c_int, c_int]),
     "boys_top_order_f64": (c_int, [c_int]),
     "boys_eval_f64": (c_int, [vp, i64, c_int, vp, vp]),
+    "boys_top_order_f32": (c_int, [c_int]),
+    "boys_eval_f32": (c_int, [vp, i64, c_int, vp, vp]),
+    "boys_eval_f64_host_workspace": (c_size, [c_int, i64]),
+    "boys_eval_f64_host": (c_int, [vp, i64, c_int, vp, vp, c_size, vp]),
+    "boys_eval_f32_host_workspace": (c_size, [c_int, i64]),
+    "boys_eval_f32_host": (c_int, [vp, i64, c_int, vp, vp, c_size, vp]),
     # include/boys_microbench.h
     "boys_microbench_launch": (c_int, [c_int, i64, vp, c_int, vp]),
     "boys_microbench_ops_per_thread_iter": (c_int, []),

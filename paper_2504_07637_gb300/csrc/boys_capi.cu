@@ -2,16 +2,23 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "boys_coeffs_f64.inc"
 #include "boys_common.cuh"
+#include "boys_f32_row.cuh"
 
 int boys_f64_dispatch_p0(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
 int boys_f64_dispatch_p1(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
 int boys_f64_dispatch_p2(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
+int boys_f32_dispatch_p0(int n_max, const float *x, int64_t count, float *out, cudaStream_t s);
+int boys_f32_dispatch_p1(int n_max, const float *x, int64_t count, float *out, cudaStream_t s);
 
 namespace {
 
 using boys::kMaxNF64;
+constexpr int kMaxNF32 = 16;  // as in boys_f32.cuh
+constexpr int f32_top_order(int n_max) { return n_max <= 8 ? n_max : n_max + 1; }
 
 // The kernels are built for sm_103a only; reject other devices up front
 // instead of failing inside a launch.
@@ -52,6 +59,103 @@ int check_rows(const void *x, int64_t count, int n_max, int max_n, const void *o
   return device_accessible(out);
 }
 
+// A second stream (and its fork/join events) per device for the host-buffer
+// pipeline, created on first use and kept for the life of the process.
+struct HelperStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+constexpr int kMaxDevices = 64;
+HelperStream g_helper[kMaxDevices];
+std::mutex g_helper_mu;
+
+int helper_for_current_device(HelperStream **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BOYS_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_helper_mu);
+  HelperStream &h = g_helper[dev];
+  if (!h.s) {
+    if (cudaStreamCreateWithFlags(&h.s, cudaStreamNonBlocking) != cudaSuccess) return BOYS_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&h.fork, cudaEventDisableTiming) != cudaSuccess) return BOYS_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&h.join, cudaEventDisableTiming) != cudaSuccess) return BOYS_ERR_CUDA;
+  }
+  *out = &h;
+  return BOYS_OK;
+}
+
+int dispatch_f64(int n_max, const double *x, int64_t count, double *out, cudaStream_t s) {
+  int rc;
+  if (n_max <= 12) rc = boys_f64_dispatch_p0(n_max, x, count, out, s);
+  else if (n_max <= 24) rc = boys_f64_dispatch_p1(n_max, x, count, out, s);
+  else rc = boys_f64_dispatch_p2(n_max, x, count, out, s);
+  return rc < 0 ? BOYS_ERR_NMAX : rc;
+}
+
+int dispatch_f32(int n_max, const float *x, int64_t count, float *out, cudaStream_t s) {
+  const int rc = n_max <= 8 ? boys_f32_dispatch_p0(n_max, x, count, out, s) : boys_f32_dispatch_p1(n_max, x, count, out, s);
+  return rc < 0 ? BOYS_ERR_NMAX : rc;
+}
+
+constexpr int64_t kHostChunkGranule = 2048;  // the kernels' tile
+
+// Host arrays streamed through a device workspace in double-buffered chunks:
+// chunk i is copied in, evaluated and copied out on stream i % 2 (the
+// caller's stream or the helper stream), so one chunk's copies (copy engines)
+// overlap the other chunk's kernel, and same-stream order protects each buffer.
+template <typename T, typename Dispatch>
+int host_pipeline(const T *x_host, int64_t count, int n_max, int max_n, T *out_host, void *workspace,
+                  size_t ws_bytes, cudaStream_t caller, Dispatch dispatch) {
+  if (count < 0) return BOYS_ERR_COUNT;
+  if (n_max < 0 || n_max > max_n) return BOYS_ERR_NMAX;
+  if (count > INT64_MAX / (n_max + 1)) return BOYS_ERR_COUNT;
+  if (count == 0) return BOYS_OK;
+  if (!x_host || !out_host || !workspace) return BOYS_ERR_NULL;
+  if ((reinterpret_cast<uintptr_t>(x_host) | reinterpret_cast<uintptr_t>(out_host)) % sizeof(T) ||
+      reinterpret_cast<uintptr_t>(workspace) % 256)
+    return BOYS_ERR_ALIGN;
+  const size_t per_arg = sizeof(T) * (size_t)(n_max + 2);
+  const int64_t chunk = (int64_t)(ws_bytes / (2 * per_arg)) / kHostChunkGranule * kHostChunkGranule;
+  if (chunk < kHostChunkGranule) return BOYS_ERR_WORKSPACE;
+  int rc = device_ok();
+  if (rc) return rc;
+  {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, workspace) != cudaSuccess) {
+      cudaGetLastError();
+      return BOYS_ERR_ARG;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return BOYS_ERR_ARG;
+  }
+  HelperStream *h = nullptr;
+  if ((rc = helper_for_current_device(&h))) return rc;
+  cudaStream_t s[2] = {caller, h->s};
+  // the helper stream starts after everything already queued on the caller's stream
+  if (cudaEventRecord(h->fork, s[0]) != cudaSuccess || cudaStreamWaitEvent(s[1], h->fork, 0) != cudaSuccess)
+    return BOYS_ERR_CUDA;
+  const int W = n_max + 1;
+  char *ws = static_cast<char *>(workspace);
+  T *xbuf[2], *obuf[2];
+  for (int b = 0; b < 2; ++b) {
+    xbuf[b] = reinterpret_cast<T *>(ws + (size_t)b * chunk * per_arg);
+    obuf[b] = xbuf[b] + chunk;
+  }
+  int64_t i = 0;
+  for (int64_t off = 0; off < count; off += chunk, ++i) {
+    const int b = (int)(i & 1);
+    const int64_t n = (count - off) < chunk ? (count - off) : chunk;
+    if (cudaMemcpyAsync(xbuf[b], x_host + off, (size_t)n * sizeof(T), cudaMemcpyDefault, s[b]) != cudaSuccess)
+      return BOYS_ERR_CUDA;
+    if ((rc = dispatch(n_max, xbuf[b], n, obuf[b], s[b]))) return rc;
+    if (cudaMemcpyAsync(out_host + off * W, obuf[b], (size_t)n * W * sizeof(T), cudaMemcpyDefault, s[b]) !=
+        cudaSuccess)
+      return BOYS_ERR_CUDA;
+  }
+  // the caller's stream completes only after the helper stream's chunks
+  if (cudaEventRecord(h->join, s[1]) != cudaSuccess || cudaStreamWaitEvent(s[0], h->join, 0) != cudaSuccess)
+    return BOYS_ERR_CUDA;
+  return BOYS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -73,12 +177,25 @@ const char *boys_status_string(int status) {
 
 int boys_max_n(int precision_bits) {
   if (precision_bits == 53) return kMaxNF64;
+  if (precision_bits == 24) return kMaxNF32;
   return -1;
 }
 
 double boys_cutoff(int n, int precision_bits) {
   if (precision_bits == 53 && n >= 0 && n <= BOYS_F64_TABLE_MAX_N) return kBoysF64CutoffHost[n];
+  if (precision_bits == 24 && n >= 0 && n <= BOYS_F32_TABLE_MAX_N) return kBoysF32CutoffHost[n];
   return NAN;
+}
+
+int boys_top_order_f32(int n_max) {
+  if (n_max < 0 || n_max > kMaxNF32) return -1;
+  return f32_top_order(n_max);
+}
+
+boys_status boys_eval_f32(const float *x, int64_t count, int n_max, float *out, void *stream) {
+  int rc = check_rows(x, count, n_max, kMaxNF32, out, sizeof(float));
+  if (rc || count == 0) return (boys_status)rc;
+  return (boys_status)dispatch_f32(n_max, x, count, out, static_cast<cudaStream_t>(stream));
 }
 
 int boys_top_order_f64(int n_max) {
@@ -89,11 +206,31 @@ int boys_top_order_f64(int n_max) {
 boys_status boys_eval_f64(const double *x, int64_t count, int n_max, double *out, void *stream) {
   int rc = check_rows(x, count, n_max, kMaxNF64, out, sizeof(double));
   if (rc || count == 0) return (boys_status)rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (n_max <= 12) rc = boys_f64_dispatch_p0(n_max, x, count, out, s);
-  else if (n_max <= 24) rc = boys_f64_dispatch_p1(n_max, x, count, out, s);
-  else rc = boys_f64_dispatch_p2(n_max, x, count, out, s);
-  return (boys_status)(rc < 0 ? BOYS_ERR_NMAX : rc);
+  return (boys_status)dispatch_f64(n_max, x, count, out, static_cast<cudaStream_t>(stream));
+}
+
+size_t boys_eval_f64_host_workspace(int n_max, int64_t chunk) {
+  if (n_max < 0 || n_max > kMaxNF64 || chunk <= 0) return 0;
+  chunk = (chunk + kHostChunkGranule - 1) / kHostChunkGranule * kHostChunkGranule;
+  return (size_t)2 * (size_t)chunk * sizeof(double) * (size_t)(n_max + 2);
+}
+
+size_t boys_eval_f32_host_workspace(int n_max, int64_t chunk) {
+  if (n_max < 0 || n_max > kMaxNF32 || chunk <= 0) return 0;
+  chunk = (chunk + kHostChunkGranule - 1) / kHostChunkGranule * kHostChunkGranule;
+  return (size_t)2 * (size_t)chunk * sizeof(float) * (size_t)(n_max + 2);
+}
+
+boys_status boys_eval_f64_host(const double *x_host, int64_t count, int n_max, double *out_host, void *workspace,
+                               size_t ws_bytes, void *stream) {
+  return (boys_status)host_pipeline<double>(x_host, count, n_max, kMaxNF64, out_host, workspace, ws_bytes,
+                                            static_cast<cudaStream_t>(stream), dispatch_f64);
+}
+
+boys_status boys_eval_f32_host(const float *x_host, int64_t count, int n_max, float *out_host, void *workspace,
+                               size_t ws_bytes, void *stream) {
+  return (boys_status)host_pipeline<float>(x_host, count, n_max, kMaxNF32, out_host, workspace, ws_bytes,
+                                           static_cast<cudaStream_t>(stream), dispatch_f32);
 }
 
 }  // extern "C"

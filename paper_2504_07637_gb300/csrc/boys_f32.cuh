@@ -1,0 +1,137 @@
+// FP32 forward path: HBM-bound (4 bytes in, 4 (n_max+1) bytes out per
+// argument), so besides splitting each tile into closed-form and asymptote
+// lists (the closed form costs ~8x the asymptote in float-float arithmetic)
+// the rows are staged in shared memory and leave as contiguous 16-byte
+// streaming stores.
+#pragma once
+
+#include "boys_common.cuh"
+#include "boys_f32_row.cuh"
+
+namespace boys {
+
+static __constant__ float kExp2Frac32ff[64] = BOYS_EXP2_FRAC32_FF;
+
+// n_top for the float path: the closed form of order n_max itself up to 8,
+// one order higher above (Sec. 3's F_{n+1} trick) to keep F_{n_max} within 2e-6.
+__host__ __device__ constexpr int f32_top_order(int n_max) { return n_max <= 8 ? n_max : n_max + 1; }
+constexpr int kMaxNF32 = 16;
+static_assert(f32_top_order(kMaxNF32) <= BOYS_F32_TABLE_MAX_N, "fitted table too short");
+
+// +-0 and 0 < x <= z by the bit pattern (negative nonzero and NaN excluded)
+__device__ __forceinline__ bool below_cutoff_f32(float v, unsigned zbits) {
+  const unsigned b = (unsigned)__float_as_int(v);
+  const unsigned mag = b & 0x7fffffffu;
+  return ((b >> 31) == 0 || mag == 0) && mag <= zbits;
+}
+
+template <int NMAX>
+struct F32Tile {
+  static constexpr int W = NMAX + 1;
+  static constexpr int TILE = W <= 9 ? 2048 : 1024;
+  static constexpr int BLOCK = 256;
+  // xs[TILE] floats, rows[TILE*W] floats, tab[64] floats, lst[TILE] u16
+  static constexpr size_t kSmem = sizeof(float) * (TILE + TILE * W + 64) + sizeof(unsigned short) * TILE;
+};
+
+template <int NMAX>
+__global__ void __launch_bounds__(256) f32_split_kernel(const float *__restrict__ x, int64_t count,
+                                                        float *__restrict__ out) {
+  using P = F32Tile<NMAX>;
+  constexpr int NTOP = f32_top_order(NMAX);
+  constexpr int W = P::W, TILE = P::TILE, BLOCK = P::BLOCK;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *rows = reinterpret_cast<float *>(smem_raw);  // 16-byte aligned, TILE*W
+  float *xs = rows + TILE * W;
+  float *tab = xs + TILE;
+  unsigned short *lst = reinterpret_cast<unsigned short *>(tab + 64);
+  __shared__ int cnt[2], next[2];
+  if (threadIdx.x < 64) tab[threadIdx.x] = kExp2Frac32ff[threadIdx.x];
+  const unsigned zbits = (unsigned)__float_as_int(BoysF32<NTOP>::kCutoff);
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t ntiles = (count + TILE - 1) / TILE;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t base = t * TILE;
+    const int nel = (int)((count - base) < TILE ? (count - base) : TILE);
+    if (threadIdx.x == 0) {
+      cnt[0] = cnt[1] = 0;
+      next[0] = next[1] = 0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int j0 = 0; j0 < TILE; j0 += BLOCK) {
+      const int j = j0 + threadIdx.x;
+      const bool valid = j < nel;
+      const float v = valid ? __ldcs(x + base + j) : 0.0f;
+      xs[j] = v;
+      const bool lo = valid && below_cutoff_f32(v, zbits);
+      const bool hi = valid && !lo;
+      const unsigned mlo = __ballot_sync(0xffffffffu, lo), mhi = __ballot_sync(0xffffffffu, hi);
+      int plo = 0, phi = 0;
+      if (lane == 0) {
+        if (mlo) plo = atomicAdd(&cnt[0], __popc(mlo));
+        if (mhi) phi = atomicAdd(&cnt[1], __popc(mhi));
+      }
+      plo = __shfl_sync(0xffffffffu, plo, 0);
+      phi = __shfl_sync(0xffffffffu, phi, 0);
+      if (lo) lst[plo + __popc(mlo & lt)] = (unsigned short)j;
+      if (hi) lst[TILE - 1 - (phi + __popc(mhi & lt))] = (unsigned short)j;
+    }
+    __syncthreads();
+    const int nlo = cnt[0], nhi = cnt[1];
+    for (;;) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(&next[0], 32);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      if (c >= nlo) break;
+      const int q = c + lane;
+      if (q < nlo) {
+        const int j = lst[q];
+        float F[W];
+        f32_formula<NTOP, NMAX>(xs[j], F, tab);
+#pragma unroll
+        for (int m = 0; m < W; ++m) rows[j * W + m] = F[m];
+      }
+    }
+    for (;;) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(&next[1], 32);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      if (c >= nhi) break;
+      const int q = c + lane;
+      if (q < nhi) {
+        const int j = lst[TILE - 1 - q];
+        float F[W];
+        f32_asymptote<NMAX>(xs[j], F);
+#pragma unroll
+        for (int m = 0; m < W; ++m) rows[j * W + m] = F[m];
+      }
+    }
+    __syncthreads();
+    store_tile<float, BLOCK>(out + base * W, rows, nel * W);
+    __syncthreads();
+  }
+}
+
+template <int NMAX>
+int launch_f32(const float *x, int64_t count, float *out, cudaStream_t s) {
+  using P = F32Tile<NMAX>;
+  auto k = f32_split_kernel<NMAX>;
+  static int grid_cap = 0;
+  if (grid_cap == 0) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::kSmem) != cudaSuccess)
+      return BOYS_ERR_CUDA;
+    grid_cap = persistent_grid(k, P::BLOCK, P::kSmem, INT64_MAX);
+  }
+  const int64_t tiles = (count + P::TILE - 1) / P::TILE;
+  const int grid = (int)(tiles < grid_cap ? tiles : grid_cap);
+  k<<<grid, P::BLOCK, P::kSmem, s>>>(x, count, out);
+  return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
+}
+
+}  // namespace boys
+
+#define BOYS_F32_CASE(k) \
+  case k:                \
+    return boys::launch_f32<k>(x, count, out, s);

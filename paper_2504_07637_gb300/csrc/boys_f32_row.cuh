@@ -1,0 +1,129 @@
+// FP32 path: the per-argument evaluation (host- and device-compilable so the
+// same code can be exercised on the CPU).
+//
+// The closed form amplifies relative errors: dF/F = -s^2 (T/D) dQ/Q with
+// s = n + 1/2, T = Q^s e^{-x}, D = x + T, which is s^2 = 72 at x -> 0 for
+// n = 8.  Plain FP32 therefore loses ~6 bits (the paper's single-precision
+// column of Table I).  Here every quantity on the amplified path -- q0 + q1 x,
+// Q^s, e^{-x}, D and D^{-s} -- is carried as a float-float pair (~48 bits),
+// while the rational part q2 x^2 u/v, whose contribution vanishes as x^2 where
+// the amplification is largest, and the recursion stay in FP32.  The fits are
+// one order N above the paper's single-precision column (~27-31 bits, cf. the
+// "about 28-bit accurate approximations" of Sec. 3), so the fit error stays
+// below FP32 rounding.
+#pragma once
+
+#include "boys_ff.cuh"
+
+#include <cstdint>
+#include <cstring>
+
+#ifdef __CUDACC__
+#define BOYS_F32_DEVFN __host__ __device__ __forceinline__
+#else
+#define BOYS_F32_DEVFN inline
+#endif
+
+BOYS_F32_DEVFN int boys_float_as_int(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_int(f);
+#else
+  int i;
+  std::memcpy(&i, &f, 4);
+  return i;
+#endif
+}
+BOYS_F32_DEVFN float boys_int_as_float(int i) {
+#ifdef __CUDA_ARCH__
+  return __int_as_float(i);
+#else
+  float f;
+  std::memcpy(&f, &i, 4);
+  return f;
+#endif
+}
+BOYS_F32_DEVFN float boys_rsqrtf(float a) {
+#ifdef __CUDA_ARCH__
+  return rsqrtf(a);
+#else
+  return 1.0f / std::sqrt(a);
+#endif
+}
+
+#include "boys_coeffs_f32.inc"
+
+namespace boys {
+
+// e^{-x} as a float-float pair for 0 <= x <= 80, by Tang's table-driven
+// method (ACM TOMS 15(2), 1989) in the float-float setting:
+//   -x = (k/32) ln2 + r,  |r| <= ln2/64,  e^{-x} = 2^(k>>5) 2^((k&31)/32) (1 + p(r)),
+// with ln2/32 split in three parts (Cody and Waite) so r is accurate to
+// 2^-31 absolute, and p(r) = r + r^2/2 + r^3/6 + r^4/24 in FP32 (truncation
+// 2^-35, rounding 2^-30 absolute).  tab holds 2^(j/32) as (hi, lo) pairs.
+BOYS_F32_DEVFN ff ff_exp_neg(float x, const float *tab) {
+  const float kShift = 12582912.0f;          // 1.5 * 2^23
+  const float kInvL = 46.16624069213867f;   // 32 / ln2
+  const float kL1 = 0.02165985107421875f;   // ln2/32 to 12 significant bits
+  const float kL2 = 9.98377799987793e-07f;  // the next 12 bits
+  const float kL3 = -5.952044412893542e-11f; // the remainder
+  float kd = fmaf(-x, kInvL, kShift);
+  const int k = boys_float_as_int(kd) - boys_float_as_int(kShift);
+  kd = kd - kShift;
+  float r = fmaf(kd, -kL1, -x);
+  r = fmaf(kd, -kL2, r);
+  r = fmaf(kd, -kL3, r);
+  float p = fmaf(r, 1.0f / 24.0f, 1.0f / 6.0f);
+  p = fmaf(r, p, 0.5f);
+  p = fmaf(r, p, 1.0f);
+  p = p * r;
+  const int j = k & 31;
+  const float th = tab[2 * j], tl = tab[2 * j + 1];
+  ff e = fast_two_sum(th, fmaf(th, p, tl + tl * p));
+  const float scale = boys_int_as_float((127 + (k >> 5)) << 23);
+  e.hi *= scale;
+  e.lo *= scale;
+  return e;
+}
+
+// Below the cut-off z_{NTOP,24}: Eqs. "pqz", "fq" and "r" (denominator read
+// as 2m-1), as in the double path.
+template <int NTOP, int NMAX>
+BOYS_F32_DEVFN void f32_formula(const float x, float (&F)[NMAX + 1], const float *tab) {
+  using Tab = BoysF32<NTOP>;
+  float u, v;
+  Tab::uv(x, u, v);
+  const float t = ((Tab::kQ2 * x) * x) * (u / v);
+  ff q = ff_add(ff{Tab::kQ0hi, Tab::kQ0lo}, ff_mul_f(ff{Tab::kQ1hi, Tab::kQ1lo}, x));
+  q = ff_add_f(q, t);
+  const ff e = ff_exp_neg(x, tab);
+  const ff T = ff_mul(ff_mul(ff_ipow<NTOP>(q), ff_sqrt(q, boys_rsqrtf(q.hi))), e);
+  const ff D = ff_add_f(T, x);
+  const ff w = ff_rcp(D, 1.0f / D.hi);
+  const ff ws = ff_sqrt(w, boys_rsqrtf(w.hi));
+  const ff fN = ff_mul(ff_mul(ff{Tab::kChi, Tab::kClo}, ff_ipow<NTOP>(w)), ws);
+  float f = fN.hi;
+  const float tx = x + x;
+#pragma unroll
+  for (int m = NTOP; m >= 1; --m) {
+    if (m <= NMAX) F[m] = f;
+    f = fmaf(tx, f, e.hi) * (1.0f / float(2 * m - 1));
+  }
+  F[0] = f;
+}
+
+// Above the cut-off (or x negative, infinite or NaN): the asymptote of
+// Eq. "limf1" built upward from F_0 = c_0 / sqrt(x).
+template <int NMAX>
+BOYS_F32_DEVFN void f32_asymptote(const float x, float (&F)[NMAX + 1]) {
+  const float rs = boys_rsqrtf(x);
+  float f = 0.886226925452758f * rs;
+  F[0] = f;
+  const float y = 1.0f / x;
+#pragma unroll
+  for (int m = 1; m <= NMAX; ++m) {
+    f = f * ((float(m) - 0.5f) * y);
+    F[m] = f;
+  }
+}
+
+}  // namespace boys

@@ -127,6 +127,85 @@ def emit_f64(table: dict) -> str:
     return "\n".join(out)
 
 
+def f(v: str) -> str:
+    """Decimal string -> C float literal (correctly rounded)."""
+    import numpy as np
+
+    r = repr(float(np.float32(float(v))))
+    if "e" not in r and "." not in r:
+        r += ".0"
+    return r + "f"
+
+
+def f_split(v: str) -> tuple[str, str]:
+    """Decimal string -> (hi, lo) float literals with hi + lo = v to ~48 bits."""
+    from decimal import Decimal, getcontext
+
+    import numpy as np
+
+    getcontext().prec = 60
+    dv = Decimal(v)
+    hi = np.float32(float(dv))
+    lo = np.float32(float(dv - Decimal(float(hi))))
+    fmt = lambda q: (repr(float(q)) + ("" if ("e" in repr(float(q)) or "." in repr(float(q))) else ".0")) + "f"
+    return fmt(hi), fmt(lo)
+
+
+def emit_f32(table: dict, source: str) -> str:
+    fits = {r["n"]: r for r in table["fits"]}
+    nmax = max(fits)
+    out = [
+        f"// Generated by paper_2504_07637_gb300/fit/emit.py from coeffs/{source}; do not edit.",
+        "// Per order n: the constrained minimax fit of Q_n for 24-bit work (Sec. 2, Eqs. pqz/pz/qz) in",
+        "// root-product form with float coefficients; q0, q1 and c_n as float-float pairs; cut-off z_{n,24}.",
+        "#pragma once",
+        f"#define BOYS_F32_TABLE_MAX_N {nmax}",
+        "",
+        "template <int N> struct BoysF32;",
+        "",
+    ]
+    host_z = []
+    for n in range(nmax + 1):
+        r = fits[n]
+        q0 = f_split(r["q0"])
+        q1 = f_split(r["q1"])
+        c = f_split(r["c"])
+        host_z.append(f(r["z"]))
+        body = ["    " + ln for ln in poly_lines("u", r["u"], fma="fmaf", ty="float", lit=f)]
+        body += ["    " + ln for ln in poly_lines("v", r["v"], fma="fmaf", ty="float", lit=f)]
+        out += [
+            f"// n = {n}: N = {r['N']}, exact-arithmetic error 2^-{r['eps_bits']:.2f}",
+            f"template <> struct BoysF32<{n}> {{",
+            f"  static constexpr int kOrderN = {r['N']};",
+            f"  static constexpr float kCutoff = {f(r['z'])};",
+            f"  static constexpr float kQ0hi = {q0[0]}, kQ0lo = {q0[1]};",
+            f"  static constexpr float kQ1hi = {q1[0]}, kQ1lo = {q1[1]};",
+            f"  static constexpr float kQ2 = {f(r['q2'])};",
+            f"  static constexpr float kChi = {c[0]}, kClo = {c[1]};",
+            "  static BOYS_FF_HD void uv(float x, float &u_out, float &v_out) {",
+            *body,
+            "    u_out = u;",
+            "    v_out = v;",
+            "  }",
+            "};",
+            "",
+        ]
+    out += [f"static const float kBoysF32CutoffHost[{nmax + 1}] = {{" + ", ".join(host_z) + "};", ""]
+    return "\n".join(out)
+
+
+def exp2_table_ff(n: int = 32) -> str:
+    """2^(j/n) as (hi, lo) float pairs, j = 0..n-1."""
+    from decimal import Decimal, getcontext
+
+    getcontext().prec = 60
+    vals = []
+    for j in range(n):
+        hi, lo = f_split(str(Decimal(2) ** (Decimal(j) / Decimal(n))))
+        vals.append(f"{hi}, {lo}")
+    return ", ".join(vals)
+
+
 def exp2_table(n: int = 64) -> str:
     """2^(j/n), j = 0..n-1, correctly rounded to double (table of Tang's
     table-driven exponential)."""
@@ -140,6 +219,9 @@ def exp2_table(n: int = 64) -> str:
     return ", ".join(vals)
 
 
+F32_SOURCE = "boys_fit_b24_plus1.json"
+
+
 def main():
     with open(os.path.join(COEFF_DIR, "boys_fit_b53.json")) as fh:
         t53 = json.load(fh)
@@ -148,6 +230,17 @@ def main():
     with open(path, "w") as fh:
         fh.write(src)
     print(f"wrote {path}")
+    f32_path = os.path.join(COEFF_DIR, F32_SOURCE)
+    if os.path.exists(f32_path):
+        with open(f32_path) as fh:
+            t24 = json.load(fh)
+        src = emit_f32(t24, F32_SOURCE)
+        src += "\n// 2^(j/32), j = 0..31, as (hi, lo) float pairs\n"
+        src += f"#define BOYS_EXP2_FRAC32_FF {{{exp2_table_ff()}}}\n"
+        path = os.path.join(CSRC, "boys_coeffs_f32.inc")
+        with open(path, "w") as fh:
+            fh.write(src)
+        print(f"wrote {path}")
 
 
 if __name__ == "__main__":

@@ -89,6 +89,7 @@ def main():
     ap.add_argument("--bits", type=int, default=53)
     ap.add_argument("--n", default="0-37")
     ap.add_argument("--N", type=int, default=0, help="override the order (0 = Table I)")
+    ap.add_argument("--N-offset", type=int, default=0, help="order = Table I's N plus this offset")
     ap.add_argument("--jobs", type=int, default=os.cpu_count() or 1)
     ap.add_argument("--out", default="")
     ap.add_argument("--seed", type=int, default=-1,
@@ -120,7 +121,7 @@ def main():
         scale = bf.cutoff(n, args.bits) / mp.mpf(src["z"])
         return [mp.nstr(mp.mpf(v) * scale, 40) for v in src["ref_x"]]
 
-    todo = [(n, args.N or table_order(n, args.bits), args.bits) for n in ns]
+    todo = [(n, args.N or table_order(n, args.bits) + args.N_offset, args.bits) for n in ns]
     todo = [(n, N, b, seed_for(n, N)) for n, N, b in todo]
     ctx = mproc.get_context("spawn")
     with ctx.Pool(args.jobs) as pool:

@@ -181,3 +181,30 @@ def test_library_exponential_against_oracle(lib):
     ref = np.exp(-x.astype(np.longdouble))
     rel = np.abs((got - ref) / ref).astype(np.float64)
     assert rel.max() < 2.5e-16, rel.max()  # about one unit in the last place
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_pipeline_matches_device_path(lib, pinned):
+    # boys_eval_f64_host streams host arrays through a small device workspace
+    # (several chunks and a ragged tail) and must give the device path's bits
+    import torch
+
+    from paper_2504_07637_gb300 import _capi, workloads
+
+    n_max, count = 8, 50_000
+    x = workloads.scale(count, seed=77)
+    dev = lib.boys(torch.from_numpy(x).cuda(), n_max).cpu().numpy()
+    xh = torch.from_numpy(x)
+    out = torch.full((count, n_max + 1), -1.0, dtype=torch.float64)
+    if pinned:
+        xh, out = xh.pin_memory(), out.pin_memory()
+    ws_bytes = _capi.load().boys_eval_f64_host_workspace(n_max, 4096)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    _capi.call("boys_eval_f64_host", xh.data_ptr(), count, n_max, out.data_ptr(), ws.data_ptr(), ws_bytes, s.cuda_stream)
+    s.synchronize()
+    assert np.array_equal(out.numpy(), dev)
+    f = _capi.load().boys_eval_f64_host
+    assert f(xh.data_ptr(), count, n_max, out.data_ptr(), ws.data_ptr(), 1000, s.cuda_stream) == 5  # too small
+    host_ws = torch.empty(ws_bytes, dtype=torch.uint8)
+    assert f(xh.data_ptr(), count, n_max, out.data_ptr(), host_ws.data_ptr(), ws_bytes, s.cuda_stream) == 7
