@@ -34,6 +34,10 @@ WORKLOADS = {
     # the float path on the same arguments rounded to float
     "scale_f32_n8": dict(count=1 << 26, n_max=8, dtype="f32"),
     "scale_f32_n16": dict(count=1 << 26, n_max=16, dtype="f32"),
+    # 4096 ragged requests (counts log-uniform on [64, 65536], n_max uniform on 0..16), graph replays
+    "ragged_f64": dict(count=0, n_max=16, dtype="f64", kind="ragged"),
+    # differentiation: 2^24 arguments, forward to n_max = 9, backward of sum_{m<=8} w_m F_m
+    "grad_f64": dict(count=1 << 24, n_max=8, dtype="f64", kind="grad"),
     # small cases of the same kernels for detailed profiling (outputs still larger than L2)
     "scale_f64_n8_small": dict(count=1 << 22, n_max=8, dtype="f64"),
     "scale_f32_n8_small": dict(count=1 << 24, n_max=8, dtype="f32"),
@@ -280,11 +284,226 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def _events_ms(fn, stream, reps):
+    """Per-call milliseconds of fn() over reps calls (CUDA events, one pair per call)."""
+    import torch
+
+    out = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def _pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(round(q / 100 * (len(v) - 1))))]
+
+
+def _f64_alu_model(capi, rates, x_host, n_max):
+    """Seconds of FP64-pipe work per argument set under the op-count model."""
+    import numpy as np
+
+    from paper_2504_07637_gb300 import roofline
+
+    lib = capi.load()
+    n_top = lib.boys_top_order_f64(n_max)
+    z = lib.boys_cutoff(n_top, 53)
+    fb = float(np.mean(x_host <= z)) if x_host.size else 0.0
+    below, above = roofline.f64_counts(n_max, n_top)
+    t = sum((fb * below[k] + (1 - fb) * above[k]) / rates[k] for k in ("fma", "div", "sqrt", "exp", "rsqrt"))
+    return t * x_host.size
+
+
+def run_ragged(args, wl):
+    """Config: 4096 ragged requests in one graph-captured call vs one plain
+    launch per request (also graph-captured), with the autotuned variant."""
+    import numpy as np
+    import torch
+
+    import paper_2504_07637_gb300 as boys
+    from paper_2504_07637_gb300 import _capi, autotune, workloads
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    x_host, offsets, n_max = workloads.ragged(4096, 16, seed=workloads.SEED_BASE + 3 + rank)
+    counts = np.diff(offsets)
+    values = int(np.sum(counts * (n_max.astype(np.int64) + 1)))
+    batch = boys.RaggedBatch(offsets, n_max, device)
+    x = torch.from_numpy(x_host).to(device)
+    out = torch.empty(batch.out_size, dtype=torch.float64, device=device)
+    tune = autotune.tune_ragged(batch, x, out, use_cache=False, reps=3)
+    variant = tune["variant"]
+    g = batch.capture(x, out, variant)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(max(args.warmup, 3)):
+        g.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    lat = _events_ms(g.replay, stream, 200)
+    # baseline: one plain launch per request, captured in one graph too
+    views = [(x[offsets[r]:offsets[r + 1]], out[batch.out_offsets_host[r]:batch.out_offsets_host[r + 1]], int(n_max[r]))
+             for r in range(n_max.size)]
+    sptr_holder = {}
+
+    def plain_all():
+        sp = torch.cuda.current_stream(device).cuda_stream
+        for xv, ov, n in views:
+            if xv.numel():
+                _capi.call("boys_eval_f64", xv.data_ptr(), xv.numel(), n, ov.data_ptr(), sp)
+
+    plain_all()
+    torch.cuda.synchronize()
+    gp = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gp):
+        plain_all()
+    for _ in range(3):
+        gp.replay()
+    torch.cuda.synchronize()
+    lat_plain = _events_ms(gp.replay, stream, 50)
+    rates = microbench(_capi, device)
+    t_alu = sum(_f64_alu_model(_capi, rates, x_host[offsets[r]:offsets[r + 1]], int(n_max[r])) for r in range(n_max.size))
+    achieved = t_alu * rates["fma"] / (ms / 1e3) / 1e12
+    peak = rates["fma"] / 1e12
+    line = {
+        "metric": METRIC,
+        "value": round(values / (ms / 1e3) / 1e9, 4),
+        "unit": "G F_m values/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": f"ragged_f64: 4096 requests, {int(offsets[-1])} arguments, {values} values, n_max uniform 0..16",
+            "variant": {"index": variant, "block": tune["all"][variant]["block"], "tile": tune["all"][variant]["tile"]},
+            "autotune_ms": {f"b{d['block']}_t{d['tile']}": d["ms"] for d in tune["all"]},
+            "l2": "output (2.7 GB) larger than L2",
+        },
+        "latency_ms": {"p50": round(_pct(lat, 50), 4), "p99": round(_pct(lat, 99), 4), "trials": len(lat)},
+        "plain_launches": {
+            "p50_ms": round(_pct(lat_plain, 50), 4),
+            "p99_ms": round(_pct(lat_plain, 99), 4),
+            "speedup_p50": round(_pct(lat_plain, 50) / _pct(lat, 50), 3),
+            "how": "4096 boys_eval_f64 calls captured in one CUDA graph",
+        },
+        "clocks": clk,
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "achieved": round(achieved, 5), "peak": round(peak, 5), "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "note": "FP64-pipe instruction equivalents (per-request op-count model) vs the measured DFMA rate"},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_grad(args, wl):
+    """Config: forward (n_max = 9) plus hand-written backward of
+    sum_{m<=8} w_m sum_i F_m(x_i) through torch.autograd."""
+    import numpy as np
+    import torch
+
+    import paper_2504_07637_gb300 as boys
+    from paper_2504_07637_gb300 import _capi, workloads
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    count, n_max = wl["count"], wl["n_max"]
+    x_host = workloads.plain(count, 53, seed=workloads.SEED_BASE + 4 + rank)
+    w = torch.from_numpy(workloads.gradient_weights(n_max)).to(device)
+    x = torch.from_numpy(x_host).to(device).requires_grad_(True)
+    stream = torch.cuda.current_stream(device)
+    gw = w.expand(count, n_max + 1)
+
+    def step():
+        F = boys.boys_autograd(x, n_max)
+        torch.autograd.backward(F, gw)
+
+    for _ in range(max(args.warmup, 3)):
+        x.grad = None
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        x.grad = None
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the pieces: forward alone (n_max + 1 = 9) and the backward kernel alone
+    xd = x.detach()
+    F = boys.boys(xd, n_max + 1)
+    fwd = _events_ms(lambda: boys.boys(xd, n_max + 1, out=F), stream, 10)
+    bwd = _events_ms(lambda: boys.boys_backward(xd, gw, n_max, F), stream, 10)
+    # central differences would need two forwards of n_max (the method's own alternative)
+    fwd8 = _events_ms(lambda: boys.boys(xd, n_max), stream, 10)
+    bwd_ms = statistics.median(bwd)
+    hbm_peak, src = measured_peaks()
+    bwd_bytes = count * 8 * (n_max + 1 + 1)  # F_1..F_{n_max+1} read, grad written (w broadcast)
+    line = {
+        "metric": METRIC,
+        "value": round(count * (n_max + 2) / (ms / 1e3) / 1e9, 4),
+        "unit": "G F_m values/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"grad_f64: 2^24 arguments, forward n_max={n_max + 1}, backward of sum_m w_m F_m, "
+                               "value counts the forward's F_m values per forward+backward step",
+                   "max_rel_err_grad": 1e-12},
+        "forward_ms": round(statistics.median(fwd), 4),
+        "backward_ms": round(bwd_ms, 4),
+        "central_difference_ms": round(2 * statistics.median(fwd8), 4),
+        "backward_speedup_vs_central_difference": round(2 * statistics.median(fwd8) / bwd_ms, 2),
+        "clocks": clk,
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "hbm", "achieved": round(bwd_bytes / (bwd_ms / 1e3) / 1e9, 1), "peak": hbm_peak,
+                     "unit": "GB/s", "frac": round(bwd_bytes / (bwd_ms / 1e3) / 1e9 / hbm_peak, 4), "traffic": None,
+                     "note": f"backward kernel: {8 * (n_max + 2)} algorithmic bytes per argument vs the {src} copy bandwidth"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)
+        return
+    if wl.get("kind") == "ragged":
+        run_ragged(args, wl)
+        return
+    if wl.get("kind") == "grad":
+        run_grad(args, wl)
         return
     import numpy as np
     import torch

@@ -89,6 +89,23 @@ int boys_top_order_f32(int n_max);
  * is within 2e-6 relative plus one subnormal unit. */
 boys_status boys_eval_f32(const float *x, int64_t count, int n_max, float *out, void *stream);
 
+/* FP64 adjoint: grad_x[i] = -sum_{m=0}^{n_max} g[i, m] F_{m+1}(x_i), the
+ * gradient of sum_{i,m} g[i, m] F_m(x_i) with respect to x_i, because
+ * differentiating Eq. "fn" under the integral gives dF_m/dx = -F_{m+1}.
+ *   x:       device, [count] doubles (read only when F is NULL)
+ *   F:       device, saved forward rows of at least n_max+2 columns
+ *            (F_0..F_{n_max+1}), row-major with leading dimension ld_F >=
+ *            n_max+2; column m+1 is read.  NULL: F_1..F_{n_max+1} are
+ *            recomputed from x with the forward kernel of order n_max+1.
+ *   g:       device; element (i, m) at g[i*g_row_stride + m*g_col_stride];
+ *            strides are in elements, >= 0 (0 broadcasts, e.g. one weight
+ *            vector shared by all rows)
+ *   grad_x:  device, [count] doubles (overwritten)
+ * n_max <= boys_max_n(53) - 1.  Relative error, normalised by
+ * sum_m |g[i,m]| F_{m+1}(x_i): 1e-12. */
+boys_status boys_eval_backward_f64(const double *x, const double *F, int64_t ld_F, const double *g, int64_t g_row_stride,
+                                   int64_t g_col_stride, int64_t count, int n_max, double *grad_x, void *stream);
+
 /* Device workspace, in bytes, that boys_eval_f64_host needs to stream chunks
  * of `chunk` arguments (rounded up to 2048) with double buffering; 0 for
  * invalid arguments. */
@@ -109,6 +126,42 @@ size_t boys_eval_f64_host_workspace(int n_max, int64_t chunk);
  * it.  Asynchronous: synchronise `stream` before reading out_host. */
 boys_status boys_eval_f64_host(const double *x_host, int64_t count, int n_max, double *out_host, void *workspace,
                                size_t ws_bytes, void *stream);
+
+/* ---- ragged batches ----------------------------------------------------
+ * R requests in one call, request r owning arguments x[offsets[r] ..
+ * offsets[r+1]) and output rows out[out_offsets[r] .. out_offsets[r+1]) with
+ * its own n_max[r] (0 <= n_max[r] <= boys_ragged_max_n()); the rows are laid
+ * out as in boys_eval_f64, so out_offsets[r+1] - out_offsets[r] must equal
+ * (offsets[r+1] - offsets[r]) * (n_max[r] + 1).  Same method and accuracy as
+ * boys_eval_f64 (bitwise the same values for the same n_max).
+ *   x:           device, x_size doubles
+ *   offsets:     device, [R+1] int64 (argument offsets, non-decreasing)
+ *   n_max:       device, [R] int32
+ *   out_offsets: device, [R+1] int64 (element offsets into out)
+ *   out:         device, out_size doubles
+ *   workspace:   device, 256-byte aligned, >= boys_ragged_workspace_bytes(R)
+ *   variant:     launch configuration (block size, tile) from
+ *                boys_ragged_variant_info, or -1 for the default; the Python
+ *                autotuner picks one by timing them
+ * The request arrays live on the device, so they are validated there: a
+ * request with a bad n_max, bad offsets or a range outside x_size/out_size
+ * produces no values; it is counted (boys_ragged_errors) and, when its
+ * output range lies inside [0, out_size), that range is filled with NaN.
+ * The call enqueues one memset and two kernels (a one-block plan and the
+ * persistent evaluation), allocates nothing and never synchronises, so it
+ * can be captured in a CUDA graph and replayed. */
+size_t boys_ragged_workspace_bytes(int32_t num_requests);
+int boys_ragged_max_n(void);
+int boys_ragged_num_variants(void);
+boys_status boys_ragged_variant_info(int variant, int *block, int *tile);
+boys_status boys_eval_ragged_f64(const double *x, int64_t x_size, const int64_t *offsets, const int32_t *n_max,
+                                 const int64_t *out_offsets, int32_t num_requests, double *out, int64_t out_size,
+                                 void *workspace, size_t ws_bytes, int variant, void *stream);
+
+/* Number of invalid requests seen by the last boys_eval_ragged_f64 that used
+ * this workspace.  Synchronises `stream` (the call that filled the
+ * workspace must have been enqueued on it or before it). */
+boys_status boys_ragged_errors(const void *workspace, int64_t *n_bad_requests, void *stream);
 
 /* Workspace size and host-buffer entry point of the float path; the same
  * contract as the double versions above, with float arrays. */

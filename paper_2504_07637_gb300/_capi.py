@@ -32,8 +32,15 @@ SIGNATURES = {
     "boys_eval_f64": (c_int, [vp, i64, c_int, vp, vp]),
     "boys_top_order_f32": (c_int, [c_int]),
     "boys_eval_f32": (c_int, [vp, i64, c_int, vp, vp]),
+    "boys_eval_backward_f64": (c_int, [vp, vp, i64, vp, i64, i64, i64, c_int, vp, vp]),
     "boys_eval_f64_host_workspace": (c_size, [c_int, i64]),
     "boys_eval_f64_host": (c_int, [vp, i64, c_int, vp, vp, c_size, vp]),
+    "boys_ragged_workspace_bytes": (c_size, [i32]),
+    "boys_ragged_max_n": (c_int, []),
+    "boys_ragged_num_variants": (c_int, []),
+    "boys_ragged_variant_info": (c_int, [c_int, vp, vp]),
+    "boys_eval_ragged_f64": (c_int, [vp, i64, vp, vp, vp, i32, vp, i64, vp, c_size, c_int, vp]),
+    "boys_ragged_errors": (c_int, [vp, vp, vp]),
     "boys_eval_f32_host_workspace": (c_size, [c_int, i64]),
     "boys_eval_f32_host": (c_int, [vp, i64, c_int, vp, vp, c_size, vp]),
     # include/boys_microbench.h

@@ -12,6 +12,12 @@ int boys_f64_dispatch_p0(int n_max, const double *x, int64_t count, double *out,
 int boys_f64_dispatch_p1(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
 int boys_f64_dispatch_p2(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
 int boys_f32_dispatch_p0(int n_max, const float *x, int64_t count, float *out, cudaStream_t s);
+int boys_grad_dispatch_p0(int n_max, const double *x, int64_t count, const double *g, int64_t g_row, int64_t g_col,
+                          double *grad, cudaStream_t s);
+int boys_grad_dispatch_p1(int n_max, const double *x, int64_t count, const double *g, int64_t g_row, int64_t g_col,
+                          double *grad, cudaStream_t s);
+int boys_grad_saved_launch(const double *F, int64_t ld_F, const double *g, int64_t g_row, int64_t g_col,
+                           int64_t count, int n_max, double *grad, cudaStream_t s);
 int boys_f32_dispatch_p1(int n_max, const float *x, int64_t count, float *out, cudaStream_t s);
 
 namespace {
@@ -207,6 +213,34 @@ boys_status boys_eval_f64(const double *x, int64_t count, int n_max, double *out
   int rc = check_rows(x, count, n_max, kMaxNF64, out, sizeof(double));
   if (rc || count == 0) return (boys_status)rc;
   return (boys_status)dispatch_f64(n_max, x, count, out, static_cast<cudaStream_t>(stream));
+}
+
+boys_status boys_eval_backward_f64(const double *x, const double *F, int64_t ld_F, const double *g, int64_t g_row_stride,
+                                   int64_t g_col_stride, int64_t count, int n_max, double *grad_x, void *stream) {
+  if (count < 0) return BOYS_ERR_COUNT;
+  if (n_max < 0 || n_max > kMaxNF64 - 1) return BOYS_ERR_NMAX;
+  if (g_row_stride < 0 || g_col_stride < 0) return BOYS_ERR_ARG;
+  if (F && ld_F < n_max + 2) return BOYS_ERR_ARG;
+  if (count == 0) return BOYS_OK;
+  if (!g || !grad_x || (!F && !x)) return BOYS_ERR_NULL;
+  if (F && count > INT64_MAX / ld_F) return BOYS_ERR_COUNT;
+  if (g_row_stride && count > INT64_MAX / g_row_stride) return BOYS_ERR_COUNT;
+  const uintptr_t bits = reinterpret_cast<uintptr_t>(g) | reinterpret_cast<uintptr_t>(grad_x) |
+                         reinterpret_cast<uintptr_t>(F) | reinterpret_cast<uintptr_t>(x);
+  if (bits % sizeof(double)) return BOYS_ERR_ALIGN;
+  int rc = device_ok();
+  if (rc) return (boys_status)rc;
+  if ((rc = device_accessible(g)) || (rc = device_accessible(grad_x))) return (boys_status)rc;
+  if ((rc = device_accessible(F ? (const void *)F : (const void *)x))) return (boys_status)rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (F) {
+    rc = boys_grad_saved_launch(F, ld_F, g, g_row_stride, g_col_stride, count, n_max, grad_x, s);
+  } else {
+    rc = n_max <= 17 ? boys_grad_dispatch_p0(n_max, x, count, g, g_row_stride, g_col_stride, grad_x, s)
+                     : boys_grad_dispatch_p1(n_max, x, count, g, g_row_stride, g_col_stride, grad_x, s);
+    if (rc < 0) rc = BOYS_ERR_NMAX;
+  }
+  return (boys_status)rc;
 }
 
 size_t boys_eval_f64_host_workspace(int n_max, int64_t chunk) {

@@ -28,7 +28,7 @@ __device__ __forceinline__ bool below_cutoff_f32(float v, unsigned zbits) {
 template <int NMAX>
 struct F32Tile {
   static constexpr int W = NMAX + 1;
-  static constexpr int TILE = W <= 9 ? 2048 : 1024;
+  static constexpr int TILE = W <= 9 ? 1024 : 512;
   static constexpr int BLOCK = 256;
   // xs[TILE] floats, rows[TILE*W] floats, tab[64] floats, lst[TILE] u16
   static constexpr size_t kSmem = sizeof(float) * (TILE + TILE * W + 64) + sizeof(unsigned short) * TILE;
@@ -51,6 +51,19 @@ __global__ void __launch_bounds__(256) f32_split_kernel(const float *__restrict_
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t ntiles = (count + TILE - 1) / TILE;
+  constexpr int PER = TILE / BLOCK;
+  // the next tile's arguments are loaded into registers while the current
+  // tile is evaluated, so the load latency hides behind the arithmetic
+  float pre[PER];
+  auto prefetch = [&](int64_t tile) {
+    const int64_t b = tile * TILE;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int64_t i = b + k * BLOCK + threadIdx.x;
+      pre[k] = (tile < ntiles && i < count) ? __ldcs(x + i) : 0.0f;
+    }
+  };
+  prefetch(blockIdx.x);
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t base = t * TILE;
     const int nel = (int)((count - base) < TILE ? (count - base) : TILE);
@@ -59,11 +72,11 @@ __global__ void __launch_bounds__(256) f32_split_kernel(const float *__restrict_
       next[0] = next[1] = 0;
     }
     __syncthreads();
-#pragma unroll 4
-    for (int j0 = 0; j0 < TILE; j0 += BLOCK) {
-      const int j = j0 + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int j = k * BLOCK + threadIdx.x;
       const bool valid = j < nel;
-      const float v = valid ? __ldcs(x + base + j) : 0.0f;
+      const float v = pre[k];
       xs[j] = v;
       const bool lo = valid && below_cutoff_f32(v, zbits);
       const bool hi = valid && !lo;
@@ -78,6 +91,7 @@ __global__ void __launch_bounds__(256) f32_split_kernel(const float *__restrict_
       if (lo) lst[plo + __popc(mlo & lt)] = (unsigned short)j;
       if (hi) lst[TILE - 1 - (phi + __popc(mhi & lt))] = (unsigned short)j;
     }
+    prefetch(t + gridDim.x);
     __syncthreads();
     const int nlo = cnt[0], nhi = cnt[1];
     for (;;) {

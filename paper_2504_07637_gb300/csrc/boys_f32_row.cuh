@@ -49,6 +49,22 @@ BOYS_F32_DEVFN float boys_rsqrtf(float a) {
   return 1.0f / std::sqrt(a);
 #endif
 }
+// a / b with a couple of ulp error (one MUFU reciprocal and a multiply)
+BOYS_F32_DEVFN float boys_fdiv_approx(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+// 1/b correctly rounded
+BOYS_F32_DEVFN float boys_frcp_rn(float b) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(b);
+#else
+  return 1.0f / b;
+#endif
+}
 
 #include "boys_coeffs_f32.inc"
 
@@ -92,13 +108,15 @@ BOYS_F32_DEVFN void f32_formula(const float x, float (&F)[NMAX + 1], const float
   using Tab = BoysF32<NTOP>;
   float u, v;
   Tab::uv(x, u, v);
-  const float t = ((Tab::kQ2 * x) * x) * (u / v);
+  // the rational part enters Q with weight ~x^2, where the amplification has
+  // fallen off: a couple of ulp in u/v cost nothing measurable
+  const float t = ((Tab::kQ2 * x) * x) * boys_fdiv_approx(u, v);
   ff q = ff_add(ff{Tab::kQ0hi, Tab::kQ0lo}, ff_mul_f(ff{Tab::kQ1hi, Tab::kQ1lo}, x));
   q = ff_add_f(q, t);
   const ff e = ff_exp_neg(x, tab);
   const ff T = ff_mul(ff_mul(ff_ipow<NTOP>(q), ff_sqrt(q, boys_rsqrtf(q.hi))), e);
   const ff D = ff_add_f(T, x);
-  const ff w = ff_rcp(D, 1.0f / D.hi);
+  const ff w = ff_rcp(D, boys_fdiv_approx(1.0f, D.hi));  // seed; the Newton step restores ~46 bits
   const ff ws = ff_sqrt(w, boys_rsqrtf(w.hi));
   const ff fN = ff_mul(ff_mul(ff{Tab::kChi, Tab::kClo}, ff_ipow<NTOP>(w)), ws);
   float f = fN.hi;
@@ -118,7 +136,7 @@ BOYS_F32_DEVFN void f32_asymptote(const float x, float (&F)[NMAX + 1]) {
   const float rs = boys_rsqrtf(x);
   float f = 0.886226925452758f * rs;
   F[0] = f;
-  const float y = 1.0f / x;
+  const float y = boys_frcp_rn(x);
 #pragma unroll
   for (int m = 1; m <= NMAX; ++m) {
     f = f * ((float(m) - 0.5f) * y);

@@ -125,92 +125,165 @@ __device__ __forceinline__ bool below_cutoff(double v, unsigned long long zbits)
   return ((b >> 63) == 0 || mag == 0) && mag <= zbits;
 }
 
-template <int NMAX, int BLOCK, int TILE>
-__global__ void __launch_bounds__(BLOCK) f64_split_kernel(const double *__restrict__ x, int64_t count,
-                                                          double *__restrict__ out) {
+// What the split kernel does with a finished row F_0..F_NMAX of argument j
+// of the current tile (j counts from the tile's first argument).
+template <int W>
+struct StoreRows {
+  double *out;  // row 0 of the tile
+  __device__ __forceinline__ void operator()(int j, const double (&F)[W]) const { store_row<W>(out + (int64_t)j * W, F); }
+};
+
+// Gradient epilogue: grad[j] = -sum_{m=0}^{W-2} g[j, m] F_{m+1}(x_j)
+// (dF_m/dx = -F_{m+1}, from differentiating Eq. "fn" under the integral).
+template <int W>
+struct GradDot {
+  const double *g;  // row 0 of the tile
+  int64_t g_row, g_col;
+  double *grad;  // element 0 of the tile
+  __device__ __forceinline__ void operator()(int j, const double (&F)[W]) const {
+    const double *gj = g + (int64_t)j * g_row;
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m + 1 < W; ++m) acc = fma(__ldg(gj + m * g_col), F[m + 1], acc);
+    grad[j] = -acc;
+  }
+};
+
+template <int TILE>
+struct F64TileSmem {
+  double xs[TILE];
+  unsigned short lst[TILE];  // below list from the front, above list from the back
+  double tab64[64];
+  int cnt[2], next[2];
+};
+
+// One tile of nel <= TILE arguments xt[0..nel): classify, build the two lists,
+// evaluate each list 32 entries per warp request and hand rows to epi.
+// All threads of the block call it; it begins and ends with a barrier.
+template <int NMAX, int BLOCK, int TILE, typename Epi>
+__device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel, const Epi &epi,
+                                         F64TileSmem<TILE> &sm) {
   constexpr int NTOP = f64_top_order(NMAX);
   constexpr int W = NMAX + 1;
   static_assert(TILE % BLOCK == 0 && TILE <= 65536, "tile");
-  __shared__ double xs[TILE];
-  __shared__ unsigned short lst[TILE];  // below list from the front, above list from the back
-  __shared__ double tab64[64];
-  __shared__ int cnt[2], next[2];
-  if (threadIdx.x < 64) tab64[threadIdx.x] = kExp2Frac64[threadIdx.x];
   const unsigned long long zbits = (unsigned long long)__double_as_longlong(BoysF64<NTOP>::kCutoff);
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
+  if (threadIdx.x == 0) {
+    sm.cnt[0] = sm.cnt[1] = 0;
+    sm.next[0] = sm.next[1] = 0;
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int j0 = 0; j0 < TILE; j0 += BLOCK) {
+    const int j = j0 + threadIdx.x;
+    const bool valid = j < nel;
+    const double v = valid ? __ldcs(xt + j) : 0.0;
+    sm.xs[j] = v;
+    const bool lo = valid && below_cutoff(v, zbits);
+    const bool hi = valid && !lo;
+    const unsigned mlo = __ballot_sync(0xffffffffu, lo), mhi = __ballot_sync(0xffffffffu, hi);
+    int plo = 0, phi = 0;
+    if (lane == 0) {
+      if (mlo) plo = atomicAdd(&sm.cnt[0], __popc(mlo));
+      if (mhi) phi = atomicAdd(&sm.cnt[1], __popc(mhi));
+    }
+    plo = __shfl_sync(0xffffffffu, plo, 0);
+    phi = __shfl_sync(0xffffffffu, phi, 0);
+    if (lo) sm.lst[plo + __popc(mlo & lt)] = (unsigned short)j;
+    if (hi) sm.lst[TILE - 1 - (phi + __popc(mhi & lt))] = (unsigned short)j;
+  }
+  __syncthreads();
+  const int nlo = sm.cnt[0], nhi = sm.cnt[1];
+  // closed form on the below-cut-off list, 32 entries per warp request
+  for (;;) {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(&sm.next[0], 32);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= nlo) break;
+    const int q = c + lane;
+    if (q < nlo) {
+      const int j = sm.lst[q];
+      double F[W];
+      f64_formula<NTOP, NMAX>(sm.xs[j], F, sm.tab64);
+      epi(j, F);
+    }
+  }
+  // asymptote on the above-cut-off list
+  for (;;) {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(&sm.next[1], 32);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= nhi) break;
+    const int q = c + lane;
+    if (q < nhi) {
+      const int j = sm.lst[TILE - 1 - q];
+      double F[W];
+      f64_asymptote<NMAX>(sm.xs[j], F);
+      epi(j, F);
+    }
+  }
+  __syncthreads();
+}
+
+template <int BLOCK, int TILE>
+__device__ __forceinline__ void f64_load_table(F64TileSmem<TILE> &sm) {
+  for (int i = threadIdx.x; i < 64; i += BLOCK) sm.tab64[i] = kExp2Frac64[i];
+}
+
+// Plain and gradient kernels: persistent blocks stride over the tiles.
+template <int NMAX, int BLOCK, int TILE, typename MakeEpi>
+__global__ void __launch_bounds__(BLOCK) f64_split_kernel(const double *__restrict__ x, int64_t count,
+                                                          const MakeEpi make) {
+  __shared__ F64TileSmem<TILE> sm;
+  f64_load_table<BLOCK, TILE>(sm);
   const int64_t ntiles = (count + TILE - 1) / TILE;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t base = t * TILE;
     const int nel = (int)((count - base) < TILE ? (count - base) : TILE);
-    if (threadIdx.x == 0) {
-      cnt[0] = cnt[1] = 0;
-      next[0] = next[1] = 0;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int j0 = 0; j0 < TILE; j0 += BLOCK) {
-      const int j = j0 + threadIdx.x;
-      const bool valid = j < nel;
-      const double v = valid ? __ldcs(x + base + j) : 0.0;
-      xs[j] = v;
-      const bool lo = valid && below_cutoff(v, zbits);
-      const bool hi = valid && !lo;
-      const unsigned mlo = __ballot_sync(0xffffffffu, lo), mhi = __ballot_sync(0xffffffffu, hi);
-      int plo = 0, phi = 0;
-      if (lane == 0) {
-        if (mlo) plo = atomicAdd(&cnt[0], __popc(mlo));
-        if (mhi) phi = atomicAdd(&cnt[1], __popc(mhi));
-      }
-      plo = __shfl_sync(0xffffffffu, plo, 0);
-      phi = __shfl_sync(0xffffffffu, phi, 0);
-      if (lo) lst[plo + __popc(mlo & lt)] = (unsigned short)j;
-      if (hi) lst[TILE - 1 - (phi + __popc(mhi & lt))] = (unsigned short)j;
-    }
-    __syncthreads();
-    const int nlo = cnt[0], nhi = cnt[1];
-    // closed form on the below-cut-off list, 32 entries per warp request
-    for (;;) {
-      int c = 0;
-      if (lane == 0) c = atomicAdd(&next[0], 32);
-      c = __shfl_sync(0xffffffffu, c, 0);
-      if (c >= nlo) break;
-      const int q = c + lane;
-      if (q < nlo) {
-        const int j = lst[q];
-        double F[W];
-        f64_formula<NTOP, NMAX>(xs[j], F, tab64);
-        store_row<W>(out + (base + j) * W, F);
-      }
-    }
-    // asymptote on the above-cut-off list
-    for (;;) {
-      int c = 0;
-      if (lane == 0) c = atomicAdd(&next[1], 32);
-      c = __shfl_sync(0xffffffffu, c, 0);
-      if (c >= nhi) break;
-      const int q = c + lane;
-      if (q < nhi) {
-        const int j = lst[TILE - 1 - q];
-        double F[W];
-        f64_asymptote<NMAX>(xs[j], F);
-        store_row<W>(out + (base + j) * W, F);
-      }
-    }
-    __syncthreads();
+    f64_tile<NMAX, BLOCK, TILE>(x + base, nel, make(base), sm);
   }
+}
+
+template <int W>
+struct MakeStore {
+  double *out;
+  __device__ __forceinline__ StoreRows<W> operator()(int64_t base) const { return StoreRows<W>{out + base * W}; }
+};
+
+template <int W>
+struct MakeGrad {
+  const double *g;
+  int64_t g_row, g_col;
+  double *grad;
+  __device__ __forceinline__ GradDot<W> operator()(int64_t base) const {
+    return GradDot<W>{g + base * g_row, g_row, g_col, grad + base};
+  }
+};
+
+constexpr int kF64Block = 256, kF64Tile = 2048;
+
+template <int NMAX, typename MakeEpi>
+int launch_f64_epi(const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s) {
+  auto k = f64_split_kernel<NMAX, kF64Block, kF64Tile, MakeEpi>;
+  static int grid_cap = 0;
+  if (grid_cap == 0) grid_cap = persistent_grid(k, kF64Block, 0, INT64_MAX);
+  const int64_t tiles = (count + kF64Tile - 1) / kF64Tile;
+  const int grid = (int)(tiles < grid_cap ? tiles : grid_cap);
+  k<<<grid, kF64Block, 0, s>>>(x, count, epi);
+  return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
 }
 
 template <int NMAX>
 int launch_f64(const double *x, int64_t count, double *out, cudaStream_t s) {
-  constexpr int BLOCK = 256, TILE = 2048;
-  auto k = f64_split_kernel<NMAX, BLOCK, TILE>;
-  static int grid_cap = 0;
-  if (grid_cap == 0) grid_cap = persistent_grid(k, BLOCK, 0, INT64_MAX);
-  const int64_t tiles = (count + TILE - 1) / TILE;
-  const int grid = (int)(tiles < grid_cap ? tiles : grid_cap);
-  k<<<grid, BLOCK, 0, s>>>(x, count, out);
-  return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
+  return launch_f64_epi<NMAX>(x, count, MakeStore<NMAX + 1>{out}, s);
+}
+
+// Backward with the forward rows recomputed: the order n_max + 1 is needed.
+template <int NMAX_FWD>
+int launch_f64_grad_recompute(const double *x, int64_t count, const double *g, int64_t g_row, int64_t g_col,
+                              double *grad, cudaStream_t s) {
+  return launch_f64_epi<NMAX_FWD>(x, count, MakeGrad<NMAX_FWD + 1>{g, g_row, g_col, grad}, s);
 }
 
 }  // namespace boys
@@ -218,3 +291,7 @@ int launch_f64(const double *x, int64_t count, double *out, cudaStream_t s) {
 #define BOYS_F64_CASE(k) \
   case k:                \
     return boys::launch_f64<k>(x, count, out, s);
+
+#define BOYS_F64_GRAD_CASE(k) \
+  case k:                     \
+    return boys::launch_f64_grad_recompute<k + 1>(x, count, g, g_row, g_col, grad, s);

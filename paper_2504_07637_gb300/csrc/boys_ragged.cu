@@ -1,0 +1,260 @@
+// Ragged batches: many requests of uneven length, each with its own n_max, in
+// one graph-capturable call.
+//
+//   memset   zero the work counter and the error counter in the workspace
+//   plan     one block validates every request and prefix-sums its tile count
+//            into the workspace (tiles never straddle two requests, so each
+//            tile has a single n_max and runs its own fully unrolled kernel body)
+//   eval     persistent blocks (resident blocks x SMs) take the next tile with a
+//            global atomic, find its request by binary search in the tile
+//            prefix (copied to shared memory), and run the FP64 tile body of
+//            the plain path for that request's n_max.  Dynamic tile stealing
+//            balances requests whose cost differs by n_max and length.
+//
+// No host synchronisation and no allocation: the call can be captured in a
+// CUDA graph and replayed.  Arguments that only the device can read (the
+// request arrays) are validated in the plan kernel; an invalid request is
+// counted in the workspace error counter and its output range, when it lies
+// inside [0, out_size), is filled with NaN.
+#include "boys_f64.cuh"
+
+namespace {
+
+constexpr int kRaggedMaxN = 16;
+constexpr int kPlanThreads = 1024;
+constexpr int kSmemPrefixMax = 16384;  // requests whose tile prefix fits in shared memory
+
+struct RaggedArgs {
+  const double *x;
+  int64_t x_size;
+  const int64_t *offsets;
+  const int32_t *n_max;
+  const int64_t *out_offsets;
+  int32_t num_requests;
+  double *out;
+  int64_t out_size;
+  int *counters;       // [1] invalid requests; [2..3] next tile (64-bit)
+  int64_t *tile_pref;  // [num_requests + 1]
+};
+
+// Workspace layout: 256 bytes of counters, then the int64 tile prefix.
+__host__ __device__ inline int64_t *prefix_of(void *ws) {
+  return reinterpret_cast<int64_t *>(static_cast<char *>(ws) + 256);
+}
+
+// Tile count of request r for a given tile size, or the NaN-fill work of an
+// invalid request; *bad = 1 for an invalid request.
+template <int TILE>
+__device__ __forceinline__ int64_t request_tiles(const RaggedArgs &a, int r, int *bad) {
+  const int64_t lo = a.offsets[r], hi = a.offsets[r + 1];
+  const int n = a.n_max[r];
+  const int64_t olo = a.out_offsets[r], ohi = a.out_offsets[r + 1];
+  const bool ok = lo >= 0 && hi >= lo && hi <= a.x_size && n >= 0 && n <= kRaggedMaxN && olo >= 0 &&
+                  ohi <= a.out_size && ohi - olo == (hi - lo) * (int64_t)(n + 1);
+  *bad = ok ? 0 : 1;
+  if (ok) return (hi - lo + TILE - 1) / TILE;
+  // invalid: fill its output range with NaN if that range is sane
+  if (olo >= 0 && ohi >= olo && ohi <= a.out_size) return (ohi - olo + (int64_t)TILE * 8 - 1) / ((int64_t)TILE * 8);
+  return 0;
+}
+
+template <int TILE>
+__global__ void __launch_bounds__(kPlanThreads) ragged_plan_kernel(const RaggedArgs a) {
+  __shared__ int64_t carry;
+  __shared__ int64_t warp_sums[kPlanThreads / 32];
+  __shared__ int bad_total;
+  if (threadIdx.x == 0) {
+    carry = 0;
+    bad_total = 0;
+    a.tile_pref[0] = 0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r0 = 0; r0 < a.num_requests; r0 += kPlanThreads) {
+    const int r = r0 + threadIdx.x;
+    int bad = 0;
+    int64_t v = r < a.num_requests ? request_tiles<TILE>(a, r, &bad) : 0;
+    if (bad) atomicAdd(&bad_total, 1);
+    // inclusive block scan: warp shuffles, then the warp totals
+    for (int d = 1; d < 32; d <<= 1) {
+      const int64_t o = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += o;
+    }
+    if (lane == 31) warp_sums[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+      int64_t w = warp_sums[lane];
+      for (int d = 1; d < 32; d <<= 1) {
+        const int64_t o = __shfl_up_sync(0xffffffffu, w, d);
+        if (lane >= d) w += o;
+      }
+      warp_sums[lane] = w;
+    }
+    __syncthreads();
+    const int64_t incl = v + (warp ? warp_sums[warp - 1] : 0) + carry;
+    if (r < a.num_requests) a.tile_pref[r + 1] = incl;
+    __syncthreads();
+    if (threadIdx.x == kPlanThreads - 1) carry = incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.counters[1] = bad_total;
+}
+
+template <int BLOCK, int TILE>
+struct RaggedSmem {
+  boys::F64TileSmem<TILE> tile;
+  int64_t cur;
+};
+
+template <int NMAX, int BLOCK, int TILE>
+__device__ __forceinline__ void ragged_tile(const RaggedArgs &a, int r, int64_t k, boys::F64TileSmem<TILE> &sm) {
+  const int64_t lo = a.offsets[r] + k * TILE;
+  const int64_t hi = a.offsets[r + 1];
+  const int nel = (int)((hi - lo) < TILE ? (hi - lo) : TILE);
+  double *rows = a.out + a.out_offsets[r] + (k * TILE) * (NMAX + 1);
+  boys::f64_tile<NMAX, BLOCK, TILE>(a.x + lo, nel, boys::StoreRows<NMAX + 1>{rows}, sm);
+}
+
+template <int BLOCK, int TILE>
+__global__ void __launch_bounds__(BLOCK) ragged_eval_kernel(const RaggedArgs a) {
+  __shared__ RaggedSmem<BLOCK, TILE> sm;
+  extern __shared__ int64_t pref_s[];  // tile prefix when it fits, else unused
+  boys::f64_load_table<BLOCK, TILE>(sm.tile);
+  const int R = a.num_requests;
+  const bool in_smem = R < kSmemPrefixMax;
+  if (in_smem)
+    for (int i = threadIdx.x; i <= R; i += BLOCK) pref_s[i] = a.tile_pref[i];
+  __syncthreads();
+  const int64_t *pref = in_smem ? pref_s : a.tile_pref;
+  const int64_t total = pref[R];
+  for (;;) {
+    if (threadIdx.x == 0) sm.cur = atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + 2), 1ULL);
+    __syncthreads();
+    const int64_t t = sm.cur;
+    __syncthreads();
+    if (t >= total) break;
+    // request r with pref[r] <= t < pref[r+1]
+    int lo = 0, hi = R;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pref[mid] <= t) lo = mid;
+      else hi = mid;
+    }
+    const int r = lo;
+    const int64_t k = t - pref[r];
+    int bad = 0;
+    request_tiles<TILE>(a, r, &bad);
+    if (bad) {
+      // NaN over this slice of the invalid request's output range
+      const int64_t olo = a.out_offsets[r] + k * (int64_t)TILE * 8;
+      const int64_t ohi = a.out_offsets[r + 1];
+      const int64_t end = (ohi - olo) < (int64_t)TILE * 8 ? ohi : olo + (int64_t)TILE * 8;
+      for (int64_t i = olo + threadIdx.x; i < end; i += BLOCK) a.out[i] = __longlong_as_double(0x7ff8000000000000LL);
+      continue;
+    }
+    switch (a.n_max[r]) {
+#define BOYS_RAGGED_CASE(n) \
+  case n:                   \
+    ragged_tile<n, BLOCK, TILE>(a, r, k, sm.tile); \
+    break;
+      BOYS_RAGGED_CASE(0) BOYS_RAGGED_CASE(1) BOYS_RAGGED_CASE(2) BOYS_RAGGED_CASE(3) BOYS_RAGGED_CASE(4)
+      BOYS_RAGGED_CASE(5) BOYS_RAGGED_CASE(6) BOYS_RAGGED_CASE(7) BOYS_RAGGED_CASE(8) BOYS_RAGGED_CASE(9)
+      BOYS_RAGGED_CASE(10) BOYS_RAGGED_CASE(11) BOYS_RAGGED_CASE(12) BOYS_RAGGED_CASE(13) BOYS_RAGGED_CASE(14)
+      BOYS_RAGGED_CASE(15) BOYS_RAGGED_CASE(16)
+#undef BOYS_RAGGED_CASE
+      default:
+        break;
+    }
+  }
+}
+
+// Launch configurations the autotuner chooses from: (block, tile).
+template <int BLOCK, int TILE>
+int launch_ragged(const RaggedArgs &a, cudaStream_t s) {
+  if (cudaMemsetAsync(a.counters, 0, 256, s) != cudaSuccess) return BOYS_ERR_CUDA;
+  ragged_plan_kernel<TILE><<<1, kPlanThreads, 0, s>>>(a);
+  if (cudaPeekAtLastError() != cudaSuccess) return BOYS_ERR_CUDA;
+  const size_t dyn = a.num_requests < kSmemPrefixMax ? sizeof(int64_t) * (size_t)(a.num_requests + 1) : 0;
+  auto k = ragged_eval_kernel<BLOCK, TILE>;
+  static int configured = 0;
+  if (!configured) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(int64_t) * kSmemPrefixMax)) != cudaSuccess)
+      return BOYS_ERR_CUDA;
+    configured = 1;
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BLOCK, dyn);
+  if (per_sm < 1) per_sm = 1;
+  k<<<sms * per_sm, BLOCK, dyn, s>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
+}
+
+struct Variant {
+  int block, tile;
+  int (*launch)(const RaggedArgs &, cudaStream_t);
+};
+const Variant kVariants[] = {
+    {256, 2048, launch_ragged<256, 2048>},
+    {128, 1024, launch_ragged<128, 1024>},
+    {256, 1024, launch_ragged<256, 1024>},
+    {512, 4096, launch_ragged<512, 4096>},
+    {128, 2048, launch_ragged<128, 2048>},
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+}  // namespace
+
+extern "C" {
+
+int boys_ragged_num_variants(void) { return kNumVariants; }
+
+boys_status boys_ragged_variant_info(int variant, int *block, int *tile) {
+  if (variant < 0 || variant >= kNumVariants || !block || !tile) return BOYS_ERR_ARG;
+  *block = kVariants[variant].block;
+  *tile = kVariants[variant].tile;
+  return BOYS_OK;
+}
+
+int boys_ragged_max_n(void) { return kRaggedMaxN; }
+
+size_t boys_ragged_workspace_bytes(int32_t num_requests) {
+  if (num_requests < 0) return 0;
+  return 256 + sizeof(int64_t) * ((size_t)num_requests + 1);
+}
+
+boys_status boys_eval_ragged_f64(const double *x, int64_t x_size, const int64_t *offsets, const int32_t *n_max,
+                                 const int64_t *out_offsets, int32_t num_requests, double *out, int64_t out_size,
+                                 void *workspace, size_t ws_bytes, int variant, void *stream) {
+  if (num_requests < 0 || x_size < 0 || out_size < 0) return BOYS_ERR_COUNT;
+  if (num_requests == 0) return BOYS_OK;
+  if (!offsets || !n_max || !out_offsets || !workspace || (x_size > 0 && !x) || (out_size > 0 && !out))
+    return BOYS_ERR_NULL;
+  if (ws_bytes < boys_ragged_workspace_bytes(num_requests)) return BOYS_ERR_WORKSPACE;
+  if (variant < -1 || variant >= kNumVariants) return BOYS_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(workspace) % 256) ||
+      ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(offsets) |
+        reinterpret_cast<uintptr_t>(out_offsets)) %
+       8) ||
+      (reinterpret_cast<uintptr_t>(n_max) % 4))
+    return BOYS_ERR_ALIGN;
+  RaggedArgs a{x, x_size, offsets, n_max, out_offsets, num_requests, out, out_size,
+               static_cast<int *>(workspace), prefix_of(workspace)};
+  return (boys_status)kVariants[variant < 0 ? 0 : variant].launch(a, static_cast<cudaStream_t>(stream));
+}
+
+boys_status boys_ragged_errors(const void *workspace, int64_t *n_bad_requests, void *stream) {
+  if (!workspace || !n_bad_requests) return BOYS_ERR_NULL;
+  int bad = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&bad, static_cast<const int *>(workspace) + 1, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+      cudaSuccess)
+    return BOYS_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return BOYS_ERR_CUDA;
+  *n_bad_requests = bad;
+  return BOYS_OK;
+}
+
+}  // extern "C"

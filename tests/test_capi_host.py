@@ -66,3 +66,32 @@ def test_table_metadata(capi, oracle_mod):
         assert abs(lib.boys_cutoff(n, 53) / oracle_mod.cutoff(n, 53) - 1) < 1e-13
     assert np.isnan(lib.boys_cutoff(99, 53))
     assert [lib.boys_top_order_f64(k) for k in (0, 3, 4, 8, 13, 23, 36, 37)] == [0, 3, 5, 9, 15, 26, 40, -1]
+
+
+def test_backward_host_argument_checks(capi):
+    f = capi.load().boys_eval_backward_f64
+    # (x, F, ld_F, g, g_row, g_col, count, n_max, grad, stream)
+    assert f(8, 8, 10, 8, 9, 1, -1, 8, 8, None) == 2  # count < 0
+    assert f(8, 8, 10, 8, 9, 1, 10, 36, 8, None) == 3  # needs F_{n_max+1}
+    assert f(8, 8, 10, 8, -9, 1, 10, 8, 8, None) == 7  # negative stride
+    assert f(8, 8, 9, 8, 9, 1, 10, 8, 8, None) == 7  # ld_F < n_max + 2
+    assert f(8, 8, 10, None, 9, 1, 10, 8, 8, None) == 1  # no gradient
+    assert f(None, None, 0, 8, 9, 1, 10, 8, 8, None) == 1  # neither F nor x
+    assert f(8, 8, 10, 8, 9, 1, 0, 8, 8, None) == 0  # empty
+    assert f(8, 0x1004, 10, 8, 9, 1, 10, 8, 8, None) == 4  # misaligned F
+
+
+def test_ragged_host_argument_checks(capi):
+    lib = capi.load()
+    f = lib.boys_eval_ragged_f64
+    need = lib.boys_ragged_workspace_bytes(10)
+    assert need == 256 + 8 * 11
+    # (x, x_size, offsets, n_max, out_offsets, R, out, out_size, ws, ws_bytes, variant, stream)
+    assert f(8, 10, 8, 4, 8, -1, 8, 10, 256, need, -1, None) == 2  # R < 0
+    assert f(8, 10, 8, 4, 8, 0, 8, 10, 256, need, -1, None) == 0  # empty batch
+    assert f(8, 10, 8, 4, 8, 10, 8, 10, 256, need - 8, -1, None) == 5  # workspace too small
+    assert f(8, 10, 8, 4, 8, 10, 8, 10, 256, need, 99, None) == 7  # no such variant
+    assert f(8, 10, 8, 4, 8, 10, 8, 10, 264, need, -1, None) == 4  # workspace not 256-aligned
+    assert f(8, 10, None, 4, 8, 10, 8, 10, 256, need, -1, None) == 1  # missing offsets
+    assert lib.boys_ragged_max_n() == 16
+    assert lib.boys_ragged_num_variants() >= 2

@@ -206,5 +206,6 @@ def test_host_pipeline_matches_device_path(lib, pinned):
     assert np.array_equal(out.numpy(), dev)
     f = _capi.load().boys_eval_f64_host
     assert f(xh.data_ptr(), count, n_max, out.data_ptr(), ws.data_ptr(), 1000, s.cuda_stream) == 5  # too small
-    host_ws = torch.empty(ws_bytes, dtype=torch.uint8)
-    assert f(xh.data_ptr(), count, n_max, out.data_ptr(), host_ws.data_ptr(), ws_bytes, s.cuda_stream) == 7
+    host_ws = torch.empty(ws_bytes + 256, dtype=torch.uint8)
+    hp = host_ws.data_ptr() + (-host_ws.data_ptr()) % 256  # aligned, but host memory
+    assert f(xh.data_ptr(), count, n_max, out.data_ptr(), hp, ws_bytes, s.cuda_stream) == 7
