@@ -509,7 +509,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2504_07637_gb300 import _capi, roofline, workloads
+    from paper_2504_07637_gb300 import _capi, roofline, shard, workloads
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -521,7 +521,7 @@ def main():
     f32 = wl["dtype"] == "f32"
     np_t, th_t, esz = (np.float32, torch.float32, 4) if f32 else (np.float64, torch.float64, 8)
     fn = "boys_eval_f32" if f32 else "boys_eval_f64"
-    x_host = workloads.scale(count, seed=workloads.SEED_BASE + 1 + rank).astype(np_t)
+    x_host = workloads.scale(count, seed=shard.shard_seed(workloads.SEED_BASE + 1, rank)).astype(np_t)
     x = torch.from_numpy(x_host).to(device)
     out = torch.empty((count, n_max + 1), dtype=th_t, device=device)
     stream = torch.cuda.current_stream(device)
@@ -549,10 +549,7 @@ def main():
     if ws > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device=device)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = shard.max_over_ranks(ms, device)
     values_per_step = count * (n_max + 1) * ws
     value = values_per_step / (ms_max / 1e3) / 1e9
     launches = args.steps  # one kernel per evaluation call
