@@ -158,6 +158,32 @@ boys_status boys_eval_ragged_f64(const double *x, int64_t x_size, const int64_t 
                                  const int64_t *out_offsets, int32_t num_requests, double *out, int64_t out_size,
                                  void *workspace, size_t ws_bytes, int variant, void *stream);
 
+/* Ragged evaluation for callers that cannot provide device scratch memory.
+ *
+ * The paper has no counterpart; this is a convenience of the library.
+ * Callers that cannot allocate device memory -- e.g. a host whose device
+ * memory is all held by its own pool and that forbids libraries from calling
+ * cudaMalloc, or code with no device allocator at hand -- cannot pass the
+ * workspace boys_eval_ragged_f64 needs.  This entry point takes the same
+ * arguments minus the workspace and uses a fixed scratch array compiled into
+ * the library instead; it calls no allocation routine.
+ *   - At most BOYS_RAGGED_NOALLOC_MAX_REQUESTS requests (the array holds the
+ *     counters and the tile prefix for that many: about 512 KiB); more
+ *     returns BOYS_ERR_WORKSPACE before anything is launched.
+ *   - The array exists once per GPU that loads the library and stays
+ *     allocated until the process exits.
+ *   - The first call on a device looks up the array's device address (a
+ *     one-time set-up per device, done with that device current); make that
+ *     first call before any stream capture.
+ *   - Every call shares the array, which keeps the last call's contents; the
+ *     call clears what must start at zero itself.  Calls whose work overlaps
+ *     on the GPU race on the array: order them (e.g. one stream).
+ * Results are those of boys_eval_ragged_f64. */
+#define BOYS_RAGGED_NOALLOC_MAX_REQUESTS 65536
+boys_status boys_eval_ragged_f64_noalloc(const double *x, int64_t x_size, const int64_t *offsets, const int32_t *n_max,
+                                         const int64_t *out_offsets, int32_t num_requests, double *out,
+                                         int64_t out_size, int variant, void *stream);
+
 /* Number of invalid requests seen by the last boys_eval_ragged_f64 that used
  * this workspace.  Synchronises `stream` (the call that filled the
  * workspace must have been enqueued on it or before it). */

@@ -41,6 +41,7 @@ SIGNATURES = {
     "boys_ragged_variant_info": (c_int, [c_int, vp, vp]),
     "boys_eval_ragged_f64": (c_int, [vp, i64, vp, vp, vp, i32, vp, i64, vp, c_size, c_int, vp]),
     "boys_ragged_errors": (c_int, [vp, vp, vp]),
+    "boys_eval_ragged_f64_noalloc": (c_int, [vp, i64, vp, vp, vp, i32, vp, i64, c_int, vp]),
     "boys_eval_f32_host_workspace": (c_size, [c_int, i64]),
     "boys_eval_f32_host": (c_int, [vp, i64, c_int, vp, vp, c_size, vp]),
     # include/boys_microbench.h

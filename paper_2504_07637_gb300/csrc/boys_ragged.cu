@@ -16,6 +16,8 @@
 // request arrays) are validated in the plan kernel; an invalid request is
 // counted in the workspace error counter and its output range, when it lies
 // inside [0, out_size), is filled with NaN.
+#include <mutex>
+
 #include "boys_f64.cuh"
 
 namespace {
@@ -258,3 +260,68 @@ boys_status boys_ragged_errors(const void *workspace, int64_t *n_bad_requests, v
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Ragged evaluation without a caller-provided workspace.
+//
+// Some callers cannot hand the library device scratch memory: for example a
+// host application whose device memory is all owned by its own pool and that
+// forbids libraries from calling cudaMalloc (an allocation can synchronise
+// the device and fragments the pool), or code running where no device
+// allocator is available to it.  For them the counters and tile prefix live
+// in one fixed array in the library's device image.  The array exists once
+// per GPU that loads the library and stays allocated until the process
+// exits; every call shares it, so calls whose work overlaps on the GPU race
+// on it and must be ordered by the caller (for example, issued on one
+// stream).
+
+namespace {
+
+constexpr int32_t kNoAllocMaxRequests = BOYS_RAGGED_NOALLOC_MAX_REQUESTS;
+constexpr size_t kNoAllocScratchBytes = 256 + sizeof(int64_t) * ((size_t)kNoAllocMaxRequests + 1);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+void *g_noalloc_addr[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device.  The name
+// g_noalloc_scratch is only a host-side stand-in in host code, so the real
+// address is looked up once per device, with that device current.
+int noalloc_scratch(void **addr) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return BOYS_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return BOYS_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *addr = g_noalloc_addr[dev];
+  return BOYS_OK;
+}
+
+}  // namespace
+
+extern "C" boys_status boys_eval_ragged_f64_noalloc(const double *x, int64_t x_size, const int64_t *offsets,
+                                                    const int32_t *n_max, const int64_t *out_offsets,
+                                                    int32_t num_requests, double *out, int64_t out_size, int variant,
+                                                    void *stream) {
+  if (num_requests > kNoAllocMaxRequests) return BOYS_ERR_WORKSPACE;
+  if (num_requests <= 0) {
+    return boys_eval_ragged_f64(x, x_size, offsets, n_max, out_offsets, num_requests, out, out_size, nullptr, 0,
+                                variant, stream);
+  }
+  void *scratch = nullptr;
+  const int rc = noalloc_scratch(&scratch);
+  if (rc) return (boys_status)rc;
+  // the counters that must start at zero are cleared by the launch itself
+  // (a memset of the first 256 bytes), and the plan kernel rewrites the
+  // tile prefix, so nothing of the previous call's contents is used
+  return boys_eval_ragged_f64(x, x_size, offsets, n_max, out_offsets, num_requests, out, out_size, scratch,
+                              kNoAllocScratchBytes, variant, stream);
+}
