@@ -72,4 +72,28 @@ __device__ __forceinline__ void store_tile(T *__restrict__ dst, const T *__restr
   }
 }
 
+// ---- asynchronous bulk copies (the TMA engine, sm_90 and later) ----------
+// A bulk copy moves a contiguous block between shared and global memory
+// without the threads: both addresses 16-byte aligned, size a multiple of 16.
+
+// Writes made to shared memory by ordinary stores become visible to the bulk
+// copy engine only after this fence (executed by the writing threads, then a
+// barrier).
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Start copying `bytes` from shared memory to global memory (one thread).
+__device__ __forceinline__ void bulk_store_s2g(void *gdst, const void *ssrc, unsigned bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(ssrc);
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gdst), "r"(s), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+
+// Wait until every bulk copy this thread started has finished reading its
+// shared-memory source (the source may then be overwritten).
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+
+// Wait until every bulk copy this thread started has completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
 }  // namespace boys
