@@ -319,7 +319,7 @@ def _f64_alu_model(capi, rates, x_host, n_max):
     return t * x_host.size
 
 
-def run_ragged(args, wl):
+def run_ragged(args, wl, emit=True):
     """Config: 4096 ragged requests in one graph-captured call vs one plain
     launch per request (also graph-captured), with the autotuned variant."""
     import numpy as np
@@ -412,10 +412,12 @@ def run_ragged(args, wl):
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "note": "FP64-pipe instruction equivalents (per-request op-count model) vs the measured DFMA rate"},
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_grad(args, wl):
+def run_grad(args, wl, emit=True):
     """Config: forward (n_max = 9) plus hand-written backward of
     sum_{m<=8} w_m sum_i F_m(x_i) through torch.autograd."""
     import numpy as np
@@ -490,7 +492,138 @@ def run_grad(args, wl):
                      "unit": "GB/s", "frac": round(bwd_bytes / (bwd_ms / 1e3) / 1e9 / hbm_peak, 4), "traffic": None,
                      "note": f"backward kernel: {8 * (n_max + 2)} algorithmic bytes per argument vs the {src} copy bandwidth"},
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks_index=None):
+    """Time one scale-workload configuration; returns its figures.
+
+    The timed region is exactly `steps` evaluation calls on the current
+    stream, bracketed by CUDA events; the arguments (2^26 of them, 256 or
+    512 MB) and the output exceed the L2, so no flush is needed."""
+    import numpy as np
+    import torch
+
+    from paper_2504_07637_gb300 import _capi, roofline, workloads
+
+    n_max, count = wl["n_max"], wl["count"]
+    f32 = wl["dtype"] == "f32"
+    np_t, th_t, esz = (np.float32, torch.float32, 4) if f32 else (np.float64, torch.float64, 8)
+    fn = "boys_eval_f32" if f32 else "boys_eval_f64"
+    x_host = workloads.scale(count, seed=seed).astype(np_t)
+    x = torch.from_numpy(x_host).to(device)
+    out = torch.empty((count, n_max + 1), dtype=th_t, device=device)
+    stream = torch.cuda.current_stream(device)
+    sptr = stream.cuda_stream
+
+    def step():
+        _capi.call(fn, x.data_ptr(), count, n_max, out.data_ptr(), sptr)
+
+    for _ in range(max(warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(clocks_index) if clocks_index is not None else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1) / steps
+    res = {"ms": ms, "values": count * (n_max + 1), "clocks": clk, "x_host": x_host}
+    hbm_peak, hbm_src = measured_peaks()
+    hbm_gbs = roofline.bytes_per_arg(n_max, esz) * count / (ms / 1e3) / 1e9
+    if not f32 and rates is not None:
+        n_top = _capi.load().boys_top_order_f64(n_max)
+        z = _capi.load().boys_cutoff(n_top, 53)
+        fb = float(np.mean(x_host <= z))
+        below, above = roofline.f64_counts(n_max, n_top)
+        t_arg = sum((fb * below[k] + (1 - fb) * above[k]) / rates[k] for k in ("fma", "div", "sqrt", "exp", "rsqrt"))
+        achieved = t_arg * rates["fma"] * count / (ms / 1e3) / 1e12
+        peak = rates["fma"] / 1e12
+        res["roofline"] = {
+            "bound": "alu",
+            "achieved": round(achieved, 5),
+            "peak": round(peak, 5),
+            "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": traffic_record(f"f64_split_kernel<{n_max}>/scale_2^26"),
+            "note": "FP64-pipe instruction equivalents per second (1 per add/mul/fma; exp, sqrt, rsqrt and div "
+            "weighted by their measured cost) vs the DFMA rate measured in this run; "
+            f"{fb:.3f} of arguments below z_{{{n_top},53}}",
+            "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 4),
+                    "peak_source": hbm_src},
+            "measured_rates_gops": {k: round(v / 1e9, 2) for k, v in rates.items()},
+        }
+    elif f32:
+        n_top = _capi.load().boys_top_order_f32(n_max)
+        z = _capi.load().boys_cutoff(n_top, 24)
+        res["roofline"] = {
+            "bound": "hbm",
+            "achieved": round(hbm_gbs, 1),
+            "peak": hbm_peak,
+            "unit": "GB/s",
+            "frac": round(hbm_gbs / hbm_peak, 4),
+            "traffic": traffic_record(f"f32_split_kernel<{n_max}>/scale_2^26"),
+            "note": f"{roofline.bytes_per_arg(n_max, esz)} algorithmic bytes per argument (x in, n_max+1 floats out) "
+            f"vs the {hbm_src} copy bandwidth; {float(np.mean(x_host <= z)):.3f} of arguments below z_{{{n_top},24}}",
+        }
+    if e2e:
+        # end to end through the C ABI with host buffers: pinned host arrays are
+        # streamed through a device workspace in chunks whose copies overlap
+        # the neighbouring chunk's kernel
+        xp = torch.from_numpy(x_host).pin_memory()
+        op = torch.empty((count, n_max + 1), dtype=th_t, pin_memory=True)
+        ws_bytes = 1 << 30
+        wsp = torch.empty(ws_bytes, dtype=torch.uint8, device=device)
+
+        def e2e_step():
+            _capi.call(fn + "_host", xp.data_ptr(), count, n_max, op.data_ptr(), wsp.data_ptr(), ws_bytes, sptr)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        k2 = max(2, min(steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            e2e_step()
+            stream.synchronize()
+        dt = (time.perf_counter() - t0) / k2
+        res["e2e"] = {
+            "value": round(count * (n_max + 1) / dt / 1e9, 4),
+            "unit": "G F_m values/s",
+            "h2d_bytes_per_step": esz * count,
+            "d2h_bytes_per_step": esz * count * (n_max + 1),
+            "how": f"{fn}_host: pinned host in/out, 1 GiB device workspace, chunked copies overlapped with "
+            "compute; host wall clock",
+        }
+        del xp, op, wsp
+    del x, out
+    torch.cuda.empty_cache()
+    return res
+
+
+def measure_plain(device, rates):
+    """The plain 65,536-argument FP64 workload (n_max = 8): one launch, median of 50."""
+    import torch
+
+    from paper_2504_07637_gb300 import _capi, workloads
+
+    x = torch.from_numpy(workloads.plain(65536, 53)).to(device)
+    out = torch.empty((65536, 9), dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+    f = lambda: _capi.call("boys_eval_f64", x.data_ptr(), 65536, 8, out.data_ptr(), stream.cuda_stream)
+    for _ in range(5):
+        f()
+    ms = statistics.median(_events_ms(f, stream, 50))
+    return {"value": round(65536 * 9 / (ms / 1e3) / 1e9, 3), "ms_per_launch": round(ms, 5),
+            "note": "one launch over 65,536 arguments (32 tiles: well under one wave of the GPU)"}
 
 
 def main():
@@ -505,11 +638,10 @@ def main():
     if wl.get("kind") == "grad":
         run_grad(args, wl)
         return
-    import numpy as np
     import torch
     import torch.distributed as dist
 
-    from paper_2504_07637_gb300 import _capi, roofline, shard, workloads
+    from paper_2504_07637_gb300 import _capi, shard, workloads
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -518,119 +650,44 @@ def main():
     device = torch.device("cuda", local)
     _capi.load()
     n_max, count = wl["n_max"], wl["count"]
-    f32 = wl["dtype"] == "f32"
-    np_t, th_t, esz = (np.float32, torch.float32, 4) if f32 else (np.float64, torch.float64, 8)
-    fn = "boys_eval_f32" if f32 else "boys_eval_f64"
-    x_host = workloads.scale(count, seed=shard.shard_seed(workloads.SEED_BASE + 1, rank)).astype(np_t)
-    x = torch.from_numpy(x_host).to(device)
-    out = torch.empty((count, n_max + 1), dtype=th_t, device=device)
-    stream = torch.cuda.current_stream(device)
-    sptr = stream.cuda_stream
-
-    def step():
-        _capi.call(fn, x.data_ptr(), count, n_max, out.data_ptr(), sptr)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
+    seed = shard.shard_seed(workloads.SEED_BASE + 1, rank)
     if ws > 1:
         dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    if ws > 1:
-        dist.barrier()
-    ms = e0.elapsed_time(e1) / args.steps
+    rates = None if args.no_extras or wl["dtype"] == "f32" else microbench(_capi, device)
+    main_res = measure_scale(wl, args.steps, args.warmup, device, seed, rates=rates, e2e=not args.no_extras,
+                             clocks_index=local)
+    ms = main_res["ms"]
     ms_max = shard.max_over_ranks(ms, device)
-    values_per_step = count * (n_max + 1) * ws
-    value = values_per_step / (ms_max / 1e3) / 1e9
-    launches = args.steps  # one kernel per evaluation call
-
+    value = main_res["values"] * ws / (ms_max / 1e3) / 1e9
     extras = {}
-    hbm_peak, hbm_src = measured_peaks()
-    hbm_bytes = roofline.bytes_per_arg(n_max, esz) * count
-    hbm_gbs = hbm_bytes / (ms / 1e3) / 1e9
-    if not args.no_extras and not f32:
-        # ALU roofline from live microbenchmarks of the FP64 operations
-        rates = microbench(_capi, device)
-        n_top = _capi.load().boys_top_order_f64(n_max)
-        z = _capi.load().boys_cutoff(n_top, 53)
-        frac_below = float(np.mean(x_host <= z))
-        below, above = roofline.f64_counts(n_max, n_top)
-        t_arg = sum(
-            (frac_below * below[k] + (1 - frac_below) * above[k]) / rates[k] for k in ("fma", "div", "sqrt", "exp", "rsqrt")
-        )
-        fma_equiv = t_arg * rates["fma"]  # FP64-pipe instruction equivalents per argument
-        achieved = fma_equiv * count / (ms / 1e3) / 1e12
-        peak = rates["fma"] / 1e12
-        traffic = traffic_record(f"f64_split_kernel<{n_max}>/scale_2^26")
-        extras["roofline"] = {
-            "bound": "alu",
-            "achieved": round(achieved, 5),
-            "peak": round(peak, 5),
-            "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4),
-            "traffic": traffic,
-            "note": "FP64-pipe instruction equivalents per second (1 per add/mul/fma; exp, sqrt, rsqrt and div "
-            "weighted by their measured cost) vs the DFMA rate measured in this run; "
-            f"{frac_below:.3f} of arguments below z_{{{n_top},53}}",
-            "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 4),
-                    "peak_source": hbm_src},
-            "measured_rates_gops": {k: round(v / 1e9, 2) for k, v in rates.items()},
-        }
-    elif not args.no_extras:
-        n_top = _capi.load().boys_top_order_f32(n_max)
-        z = _capi.load().boys_cutoff(n_top, 24)
-        extras["roofline"] = {
-            "bound": "hbm",
-            "achieved": round(hbm_gbs, 1),
-            "peak": hbm_peak,
-            "unit": "GB/s",
-            "frac": round(hbm_gbs / hbm_peak, 4),
-            "traffic": traffic_record(f"f32_split_kernel<{n_max}>/scale_2^26"),
-            "note": f"{roofline.bytes_per_arg(n_max, esz)} algorithmic bytes per argument (x in, n_max+1 floats out) "
-            f"vs the {hbm_src} copy bandwidth; {float(np.mean(x_host <= z)):.3f} of arguments below z_{{{n_top},24}}",
-        }
-    if not args.no_extras:
-        # end to end through the C ABI with host buffers: pinned host arrays are
-        # streamed through a device workspace in chunks whose copies overlap
-        # the neighbouring chunk's kernel (boys_eval_f64_host)
-        xp = torch.from_numpy(x_host).pin_memory()
-        op = torch.empty((count, n_max + 1), dtype=th_t, pin_memory=True)
-        ws_bytes = 1 << 30
-        wsp = torch.empty(ws_bytes, dtype=torch.uint8, device=device)
-        how = f"{fn}_host: pinned host in/out, 1 GiB device workspace, chunked copies overlapped with compute; host wall clock"
-
-        def e2e_step():
-            _capi.call(fn + "_host", xp.data_ptr(), count, n_max, op.data_ptr(), wsp.data_ptr(), ws_bytes, sptr)
-
-        e2e_step()
-        torch.cuda.synchronize()
-        k2 = max(2, min(args.steps, 5))
-        t0 = time.perf_counter()
-        for _ in range(k2):
-            e2e_step()
-            stream.synchronize()
-        dt = (time.perf_counter() - t0) / k2
-        extras["e2e"] = {
-            "value": round(count * (n_max + 1) * ws / dt / 1e9, 4),
-            "unit": "G F_m values/s",
-            "h2d_bytes_per_step": esz * count,
-            "d2h_bytes_per_step": esz * count * (n_max + 1),
-            "how": how,
-        }
-        del xp, op, wsp
+    if "roofline" in main_res:
+        extras["roofline"] = main_res["roofline"]
+    if "e2e" in main_res:
+        e = dict(main_res["e2e"])
+        e["value"] = round(e["value"] * ws, 4)
+        extras["e2e"] = e
+    # the other configurations, summarised in the same line (single GPU, default run only)
+    if ws == 1 and not args.no_extras and args.workload == "scale_f64_n8":
+        suite = {"plain_f64_n8_65536": measure_plain(device, rates)}
+        for name in ("scale_f64_n0", "scale_f64_n4", "scale_f64_n16", "scale_f32_n8", "scale_f32_n16"):
+            r = measure_scale(WORKLOADS[name], 10, 3, device, seed, rates=rates)
+            suite[name] = {"value": round(r["values"] / (r["ms"] / 1e3) / 1e9, 4), "unit": "G F_m values/s",
+                           "ms_per_step": round(r["ms"], 4), "roofline_bound": r["roofline"]["bound"],
+                           "roofline_frac": r["roofline"]["frac"]}
+        sub = argparse.Namespace(steps=10, warmup=3, gpus=1)
+        rg = run_ragged(sub, WORKLOADS["ragged_f64"], emit=False)
+        suite["ragged_f64"] = {k: rg[k] for k in ("value", "unit", "ms_per_step", "latency_ms", "plain_launches")}
+        suite["ragged_f64"]["roofline_frac"] = rg["roofline"]["frac"]
+        suite["ragged_f64"]["variant"] = rg["config"]["variant"]
+        gr = run_grad(sub, WORKLOADS["grad_f64"], emit=False)
+        suite["grad_f64"] = {k: gr[k] for k in ("value", "unit", "ms_per_step", "forward_ms", "backward_ms",
+                                                "backward_speedup_vs_central_difference")}
+        suite["grad_f64"]["backward_roofline"] = gr["roofline"]
+        extras["workloads"] = suite
     if rank == 0 and not args.no_cpu_baseline:
-        extras["cpu_baseline"] = oracle_rate(x_host.astype(np.float64), n_max)
+        import numpy as np
 
+        extras["cpu_baseline"] = oracle_rate(main_res["x_host"].astype(np.float64), n_max)
     if rank == 0:
         line = {
             "metric": METRIC,
@@ -650,11 +707,11 @@ def main():
                 "global_batch": count * ws,
                 "n_max": n_max,
                 "max_rel_err": TOL[wl["dtype"]],
-                "l2": "inputs (512 MB) and outputs larger than the 129 MB L2; no flush needed",
+                "l2": "inputs and outputs larger than the 129 MB L2; no flush needed",
                 "parallelism": f"dp{ws} (independent shards, no collective)",
             },
-            "clocks": clk,
-            "gpu_launches": launches,
+            "clocks": main_res["clocks"],
+            "gpu_launches": args.steps,
             **extras,
         }
         print(json.dumps(line), flush=True)
