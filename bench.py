@@ -465,6 +465,7 @@ def run_grad(args, wl, emit=True):
     fwd8 = _events_ms(lambda: boys.boys(xd, n_max), stream, 10)
     bwd_ms = statistics.median(bwd)
     hbm_peak, src = measured_peaks()
+    rates = microbench(_capi, device)
     bwd_bytes = count * 8 * (n_max + 1 + 1)  # F_1..F_{n_max+1} read, grad written (w broadcast)
     line = {
         "metric": METRIC,
@@ -488,9 +489,13 @@ def run_grad(args, wl, emit=True):
         "backward_speedup_vs_central_difference": round(2 * statistics.median(fwd8) / bwd_ms, 2),
         "clocks": clk,
         "gpu_launches": 2 * args.steps,
-        "roofline": {"bound": "hbm", "achieved": round(bwd_bytes / (bwd_ms / 1e3) / 1e9, 1), "peak": hbm_peak,
-                     "unit": "GB/s", "frac": round(bwd_bytes / (bwd_ms / 1e3) / 1e9 / hbm_peak, 4), "traffic": None,
-                     "note": f"backward kernel: {8 * (n_max + 2)} algorithmic bytes per argument vs the {src} copy bandwidth"},
+        "roofline": {"bound": "alu", "achieved": round(count * (n_max + 1) / (bwd_ms / 1e3) / 1e12, 5),
+                     "peak": round(rates["fma"] / 1e12, 5), "unit": "TFLOP/s",
+                     "frac": round(count * (n_max + 1) / (bwd_ms / 1e3) / rates["fma"], 4),
+                     "traffic": traffic_record("grad_saved_kernel<8>/differentiation_2^24"),
+                     "note": f"backward kernel: n_max+1 FP64 fma per argument vs the measured DFMA rate; HBM side "
+                     f"{bwd_bytes / (bwd_ms / 1e3) / 1e9:.0f} GB/s of {hbm_peak:.0f} ({src}) for "
+                     f"{8 * (n_max + 2)} algorithmic bytes per argument"},
     }
     if emit:
         print(json.dumps(line), flush=True)
