@@ -142,3 +142,65 @@ def test_no_pole_on_positive_axis(bits):
 def test_cutoffs_match_oracle(oracle_mod, bits):
     for n, rec in _fits(bits).items():
         assert abs(float(mp.mpf(rec["z"])) / oracle_mod.cutoff(n, bits) - 1) < 1e-14
+
+
+def _roots(fac):
+    R = []
+    for y, a in fac["quad"]:
+        R += [mp.mpc(mp.mpf(y), mp.sqrt(mp.mpf(a))), mp.mpc(mp.mpf(y), -mp.sqrt(mp.mpf(a)))]
+    R += [mp.mpc(mp.mpf(y)) for y in fac["lin"]]
+    if len(fac["poly"]) > 1:
+        R += list(mp.polyroots([mp.mpf(c) for c in reversed(fac["poly"])], maxsteps=400, extraprec=400))
+    return R
+
+
+def _expand(R):
+    p = [mp.mpc(1)]
+    for r in R:
+        new = [mp.mpc(0)] * (len(p) + 1)
+        for i, c in enumerate(p):
+            new[i + 1] += c
+            new[i] -= r * c
+        p = new
+    return [mp.re(c) for c in p]
+
+
+@pytest.mark.parametrize("n", [16, 36])
+def test_root_form_beats_expanded_coefficients(n):
+    # Sec. 3: with the fitted polynomials written by their (alternating-sign)
+    # coefficients, double-precision evaluation loses accuracy fast as n grows;
+    # evaluated as root products (Eqs. "pz", "qz") it does not.
+    mp.mp.dps = 40
+    rec = _fits(53)[n]
+    cu, cv = _expand(_roots(rec["u"])), _expand(_roots(rec["v"]))
+    cud, cvd = [float(c) for c in cu], [float(c) for c in cv]
+
+    def horner(c, x):
+        acc = c[-1]
+        for k in reversed(c[:-1]):
+            acc = acc * x + k
+        return acc
+
+    def roots_form(fac, x):
+        acc = 1.0
+        if len(fac["poly"]) > 1:
+            h = x + float(fac["poly"][-2])
+            for c in reversed(fac["poly"][:-2]):
+                h = h * x + float(c)
+            acc = h
+        for y, a in fac["quad"]:
+            t = x - float(y)
+            acc *= t * t + float(a)
+        for y in fac["lin"]:
+            acc *= x - float(y)
+        return acc
+
+    z = float(mp.mpf(rec["z"]))
+    worst_h = worst_r = 0.0
+    for x in np.linspace(0.5, z, 120):
+        X = mp.mpf(float(x))
+        exact = sum(c * X**k for k, c in enumerate(cu)) / sum(c * X**k for k, c in enumerate(cv))
+        worst_h = max(worst_h, abs(float((horner(cud, x) / horner(cvd, x) - exact) / exact)))
+        worst_r = max(worst_r, abs(float((roots_form(rec["u"], x) / roots_form(rec["v"], x) - exact) / exact)))
+    assert worst_r < 4e-15
+    assert worst_h > 10 * worst_r, (worst_h, worst_r)
