@@ -41,6 +41,8 @@ WORKLOADS = {
     # small cases of the same kernels for detailed profiling (outputs still larger than L2)
     "scale_f64_n8_small": dict(count=1 << 22, n_max=8, dtype="f64"),
     "scale_f32_n8_small": dict(count=1 << 24, n_max=8, dtype="f32"),
+    "scale_f64_n16_small": dict(count=1 << 22, n_max=16, dtype="f64"),
+    "ragged_f64_small": dict(count=0, n_max=16, dtype="f64", kind="ragged", requests=256),
 }
 METRIC = "G F_m values/s at stated max rel err (FP64, FP32); % of ALU/HBM roofline"
 TOL = {"f64": 2e-14, "f32": 2e-6}
@@ -331,13 +333,17 @@ def run_ragged(args, wl, emit=True):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    x_host, offsets, n_max = workloads.ragged(4096, 16, seed=workloads.SEED_BASE + 3 + rank)
+    x_host, offsets, n_max = workloads.ragged(wl.get("requests", 4096), 16, seed=workloads.SEED_BASE + 3 + rank)
     counts = np.diff(offsets)
     values = int(np.sum(counts * (n_max.astype(np.int64) + 1)))
     batch = boys.RaggedBatch(offsets, n_max, device)
     x = torch.from_numpy(x_host).to(device)
     out = torch.empty(batch.out_size, dtype=torch.float64, device=device)
-    tune = autotune.tune_ragged(batch, x, out, use_cache=False, reps=3)
+    lean = getattr(args, "no_extras", False)  # profiling: no tuning, latency trials or per-request baseline
+    if lean:
+        tune = {"variant": 0, "all": [{"block": b, "tile": t, "ms": None} for b, t in boys.ragged_variants()]}
+    else:
+        tune = autotune.tune_ragged(batch, x, out, use_cache=False, reps=3)
     variant = tune["variant"]
     g = batch.capture(x, out, variant)
     stream = torch.cuda.current_stream(device)
@@ -355,6 +361,9 @@ def run_ragged(args, wl, emit=True):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    if lean:
+        print(json.dumps({"workload": "ragged (profiling run)", "ms_per_step": round(ms, 4)}), flush=True)
+        return None
     lat = _events_ms(g.replay, stream, 200)
     # baseline: one plain launch per request, captured in one graph too
     views = [(x[offsets[r]:offsets[r + 1]], out[batch.out_offsets_host[r]:batch.out_offsets_host[r + 1]], int(n_max[r]))
