@@ -101,6 +101,26 @@ BOYS_F32_DEVFN ff ff_exp_neg(float x, const float *tab) {
   return e;
 }
 
+// a^K for a float-float a, rounded to float: float-float up to the last
+// squaring (or multiplication), which is done in FP32 on the pair
+template <int K>
+BOYS_F32_DEVFN float f32_power_tail(ff a) {
+  if constexpr (K == 0) {
+    return 1.0f;
+  } else if constexpr (K == 1) {
+    return a.hi;
+  } else {
+    const ff h = ff_ipow<K / 2>(a);
+    // (h.hi + h.lo)^2 ~ h.hi^2 + 2 h.hi h.lo
+    const float sq = fmaf(h.hi, h.hi, 2.0f * h.hi * h.lo);
+    if constexpr (K % 2) {
+      return sq * a.hi;
+    } else {
+      return sq;
+    }
+  }
+}
+
 // Below the cut-off z_{NTOP,24}: Eqs. "pqz", "fq" and "r" (denominator read
 // as 2m-1), as in the double path.
 template <int NTOP, int NMAX>
@@ -117,16 +137,18 @@ BOYS_F32_DEVFN void f32_formula(const float x, float (&F)[NMAX + 1], const float
   const ff T = ff_mul(ff_mul(ff_ipow<NTOP>(q), ff_sqrt(q, boys_rsqrtf(q.hi))), e);
   const ff D = ff_add_f(T, x);
   const ff w = ff_rcp(D, boys_fdiv_approx(1.0f, D.hi));  // seed; the Newton step restores ~46 bits
-  const ff ws = ff_sqrt(w, boys_rsqrtf(w.hi));
-  const ff fN = ff_mul(ff_mul(ff{Tab::kChi, Tab::kClo}, ff_ipow<NTOP>(w)), ws);
-  float f = fN.hi;
+  // D^{-s} = w^NTOP sqrt(w): w carries the error of D amplified by s, so it
+  // stays float-float; the power is float-float up to its last squaring,
+  // which (with sqrt(w) and c) rounds only a few times in FP32
+  const float f = f32_power_tail<NTOP>(w) * (Tab::kChi * (w.hi * boys_rsqrtf(w.hi)));
   const float tx = x + x;
+  float fm = f;
 #pragma unroll
   for (int m = NTOP; m >= 1; --m) {
-    if (m <= NMAX) F[m] = f;
-    f = fmaf(tx, f, e.hi) * (1.0f / float(2 * m - 1));
+    if (m <= NMAX) F[m] = fm;
+    fm = fmaf(tx, fm, e.hi) * (1.0f / float(2 * m - 1));
   }
-  F[0] = f;
+  F[0] = fm;
 }
 
 // Above the cut-off (or x negative, infinite or NaN): the asymptote of
