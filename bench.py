@@ -42,6 +42,9 @@ WORKLOADS = {
     "scale_f64_n8_small": dict(count=1 << 22, n_max=8, dtype="f64"),
     "scale_f32_n8_small": dict(count=1 << 24, n_max=8, dtype="f32"),
     "scale_f64_n16_small": dict(count=1 << 22, n_max=16, dtype="f64"),
+    # fused consumer: sum_m w_m F_m(x) per argument, rows kept in registers
+    "contract_f64_n8": dict(count=1 << 26, n_max=8, dtype="f64", kind="contract"),
+    "contract_f32_n8": dict(count=1 << 26, n_max=8, dtype="f32", kind="contract"),
     "ragged_f64_small": dict(count=0, n_max=16, dtype="f64", kind="ragged", requests=256),
 }
 METRIC = "G F_m values/s at stated max rel err (FP64, FP32); % of ALU/HBM roofline"
@@ -623,6 +626,46 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
     return res
 
 
+def measure_contract(wl, steps, warmup, device, seed, rates=None):
+    """The fused consumer on the scale workload: out = sum_m w_m F_m(x)."""
+    import numpy as np
+    import torch
+
+    from paper_2504_07637_gb300 import _capi, roofline, workloads
+
+    n_max, count = wl["n_max"], wl["count"]
+    f32 = wl["dtype"] == "f32"
+    np_t, th_t, esz = (np.float32, torch.float32, 4) if f32 else (np.float64, torch.float64, 8)
+    x_host = workloads.scale(count, seed=seed).astype(np_t)
+    x = torch.from_numpy(x_host).to(device)
+    w = torch.from_numpy(workloads.gradient_weights(n_max).astype(np_t)).to(device)
+    out = torch.empty(count, dtype=th_t, device=device)
+    stream = torch.cuda.current_stream(device)
+    fn = "boys_eval_contract_f32" if f32 else "boys_eval_contract_f64"
+    f = lambda: _capi.call(fn, x.data_ptr(), count, n_max, w.data_ptr(), 0, 1, out.data_ptr(), stream.cuda_stream)
+    for _ in range(max(warmup, 3)):
+        f()
+    ms = statistics.median(_events_ms(f, stream, steps))
+    res = {"value": round(count * (n_max + 1) / (ms / 1e3) / 1e9, 4), "unit": "G F_m values/s (consumed)",
+           "ms_per_step": round(ms, 4), "bytes_per_arg": 2 * esz}
+    if not f32 and rates is not None:
+        n_top = _capi.load().boys_top_order_f64(n_max)
+        fb = float(np.mean(x_host <= _capi.load().boys_cutoff(n_top, 53)))
+        below, above = roofline.f64_counts(n_max, n_top)
+        t_arg = sum((fb * below[k] + (1 - fb) * above[k]) / rates[k] for k in ("fma", "div", "sqrt", "exp", "rsqrt"))
+        t_arg += (n_max + 1) / rates["fma"]  # the contraction's fused multiply-adds
+        res["roofline_bound"] = "alu"
+        res["roofline_frac"] = round(t_arg * count / (ms / 1e3), 4)
+    else:
+        hbm_peak, _ = measured_peaks()
+        res["roofline_bound"] = "hbm"
+        res["roofline_frac"] = round(2 * esz * count / (ms / 1e3) / 1e9 / hbm_peak, 4)
+        res["note"] = "8 bytes per argument: the fused float path is bound by instruction issue, not HBM"
+    del x, out
+    torch.cuda.empty_cache()
+    return res
+
+
 def measure_plain(device, rates):
     """The plain 65,536-argument FP64 workload (n_max = 8): one launch, median of 50."""
     import torch
@@ -651,6 +694,17 @@ def main():
         return
     if wl.get("kind") == "grad":
         run_grad(args, wl)
+        return
+    if wl.get("kind") == "contract":
+        import torch
+
+        from paper_2504_07637_gb300 import _capi, workloads
+
+        torch.cuda.set_device(0)
+        dev = torch.device("cuda", 0)
+        rates = None if wl["dtype"] == "f32" else microbench(_capi, dev)
+        print(json.dumps({"workload": args.workload, **measure_contract(wl, args.steps, args.warmup, dev,
+                                                                        workloads.SEED_BASE + 1, rates)}), flush=True)
         return
     import torch
     import torch.distributed as dist
@@ -688,6 +742,8 @@ def main():
             suite[name] = {"value": round(r["values"] / (r["ms"] / 1e3) / 1e9, 4), "unit": "G F_m values/s",
                            "ms_per_step": round(r["ms"], 4), "roofline_bound": r["roofline"]["bound"],
                            "roofline_frac": r["roofline"]["frac"]}
+        for name in ("contract_f64_n8", "contract_f32_n8"):
+            suite[name] = measure_contract(WORKLOADS[name], 10, 3, device, seed, rates=rates)
         sub = argparse.Namespace(steps=10, warmup=3, gpus=1)
         rg = run_ragged(sub, WORKLOADS["ragged_f64"], emit=False)
         suite["ragged_f64"] = {k: rg[k] for k in ("value", "unit", "ms_per_step", "latency_ms", "plain_launches")}

@@ -106,6 +106,22 @@ boys_status boys_eval_f32(const float *x, int64_t count, int n_max, float *out, 
 boys_status boys_eval_backward_f64(const double *x, const double *F, int64_t ld_F, const double *g, int64_t g_row_stride,
                                    int64_t g_col_stride, int64_t count, int n_max, double *grad_x, void *stream);
 
+/* Fused consumer: out[i] = sum_{m=0}^{n_max} c[i*c_row + m*c_col] F_m(x_i).
+ * Integral codes use the Boys values at once, as inputs of a contraction or a
+ * recurrence (Sec. 1: they are the special functions of one- and two-electron
+ * integrals over Gaussians); evaluating that contraction inside the kernel
+ * keeps the rows in registers, so only x, c and out touch memory.
+ *   x:   device, [count] arguments
+ *   c:   device coefficients; strides in elements, >= 0 (0 broadcasts one
+ *        coefficient vector over all arguments)
+ *   out: device, [count]
+ * Same method and per-F_m accuracy as boys_eval_f64 / boys_eval_f32; the
+ * contraction itself rounds in the working precision. */
+boys_status boys_eval_contract_f64(const double *x, int64_t count, int n_max, const double *c, int64_t c_row,
+                                   int64_t c_col, double *out, void *stream);
+boys_status boys_eval_contract_f32(const float *x, int64_t count, int n_max, const float *c, int64_t c_row,
+                                   int64_t c_col, float *out, void *stream);
+
 /* Device workspace, in bytes, that boys_eval_f64_host needs to stream chunks
  * of `chunk` arguments (rounded up to 2048) with double buffering; 0 for
  * invalid arguments. */

@@ -7,7 +7,7 @@ package does not import torch; the wrappers load it on first use.
 """
 from ._capi import BoysError  # noqa: F401
 
-_API = ("boys", "boys_from_host", "boys_backward", "boys_autograd", "BoysFunction", "RaggedBatch",
+_API = ("boys", "boys_contract", "boys_from_host", "boys_backward", "boys_autograd", "BoysFunction", "RaggedBatch",
         "ragged_variants", "cutoff", "max_n", "top_order_f64", "top_order_f32")
 
 

@@ -33,6 +33,8 @@ SIGNATURES = {
     "boys_top_order_f32": (c_int, [c_int]),
     "boys_eval_f32": (c_int, [vp, i64, c_int, vp, vp]),
     "boys_eval_backward_f64": (c_int, [vp, vp, i64, vp, i64, i64, i64, c_int, vp, vp]),
+    "boys_eval_contract_f64": (c_int, [vp, i64, c_int, vp, i64, i64, vp, vp]),
+    "boys_eval_contract_f32": (c_int, [vp, i64, c_int, vp, i64, i64, vp, vp]),
     "boys_eval_f64_host_workspace": (c_size, [c_int, i64]),
     "boys_eval_f64_host": (c_int, [vp, i64, c_int, vp, vp, c_size, vp]),
     "boys_ragged_workspace_bytes": (c_size, [i32]),

@@ -211,3 +211,31 @@ def ragged_variants() -> list[tuple[int, int]]:
         _capi.call("boys_ragged_variant_info", v, ctypes.addressof(b), ctypes.addressof(t))
         out.append((b.value, t.value))
     return out
+
+
+def boys_contract(x: torch.Tensor, n_max: int, c: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """out[i] = sum_m c[i, m] F_m(x_i) (c of shape [n_max+1], broadcast over
+    the arguments, or [count, n_max+1]), with the F_m kept in registers.
+    float64 or float32, following x."""
+    xf = _check_input(x, (torch.float64, torch.float32))
+    n = xf.numel()
+    if c.dtype != xf.dtype or not c.is_cuda or c.device != xf.device:
+        raise TypeError("c must be a CUDA tensor of x's dtype on x's device")
+    if c.dim() == 1:
+        if c.numel() != n_max + 1:
+            raise ValueError("c must have n_max+1 entries")
+        c_row, c_col = 0, c.stride(0)
+    elif c.dim() == 2 and c.shape == (n, n_max + 1):
+        c_row, c_col = c.stride(0), c.stride(1)
+    else:
+        raise ValueError("c must be [n_max+1] or [count, n_max+1]")
+    if c_row < 0 or c_col < 0:
+        c = c.contiguous()
+        c_row, c_col = (0, 1) if c.dim() == 1 else (c.stride(0), c.stride(1))
+    if out is None:
+        out = torch.empty(n, dtype=xf.dtype, device=xf.device)
+    fn = "boys_eval_contract_f64" if xf.dtype == torch.float64 else "boys_eval_contract_f32"
+    with torch.cuda.device(xf.device):
+        _capi.call(fn, xf.data_ptr(), n, int(n_max), c.data_ptr(), c_row, c_col, out.data_ptr(),
+                   _stream_ptr(xf.device))
+    return out

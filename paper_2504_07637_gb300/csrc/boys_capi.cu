@@ -16,6 +16,12 @@ int boys_grad_dispatch_p0(int n_max, const double *x, int64_t count, const doubl
                           double *grad, cudaStream_t s);
 int boys_grad_dispatch_p1(int n_max, const double *x, int64_t count, const double *g, int64_t g_row, int64_t g_col,
                           double *grad, cudaStream_t s);
+int boys_contract_dispatch_p0(int n_max, const double *x, int64_t count, const double *c, int64_t c_row,
+                              int64_t c_col, double *out, cudaStream_t s);
+int boys_contract_dispatch_p1(int n_max, const double *x, int64_t count, const double *c, int64_t c_row,
+                              int64_t c_col, double *out, cudaStream_t s);
+int boys_contract_f32_dispatch(int n_max, const float *x, int64_t count, const float *c, int64_t c_row, int64_t c_col,
+                               float *out, cudaStream_t s);
 int boys_grad_saved_launch(const double *F, int64_t ld_F, const double *g, int64_t g_row, int64_t g_col,
                            int64_t count, int n_max, double *grad, cudaStream_t s);
 int boys_f32_dispatch_p1(int n_max, const float *x, int64_t count, float *out, cudaStream_t s);
@@ -241,6 +247,44 @@ boys_status boys_eval_backward_f64(const double *x, const double *F, int64_t ld_
     if (rc < 0) rc = BOYS_ERR_NMAX;
   }
   return (boys_status)rc;
+}
+
+boys_status boys_eval_contract_f64(const double *x, int64_t count, int n_max, const double *c, int64_t c_row,
+                                   int64_t c_col, double *out, void *stream) {
+  if (count < 0) return BOYS_ERR_COUNT;
+  if (n_max < 0 || n_max > kMaxNF64) return BOYS_ERR_NMAX;
+  if (c_row < 0 || c_col < 0) return BOYS_ERR_ARG;
+  if (count == 0) return BOYS_OK;
+  if (!x || !c || !out) return BOYS_ERR_NULL;
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(out)) %
+      sizeof(double))
+    return BOYS_ERR_ALIGN;
+  int rc = device_ok();
+  if (rc) return (boys_status)rc;
+  if ((rc = device_accessible(x)) || (rc = device_accessible(c)) || (rc = device_accessible(out)))
+    return (boys_status)rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = n_max <= 18 ? boys_contract_dispatch_p0(n_max, x, count, c, c_row, c_col, out, s)
+                   : boys_contract_dispatch_p1(n_max, x, count, c, c_row, c_col, out, s);
+  return (boys_status)(rc < 0 ? BOYS_ERR_NMAX : rc);
+}
+
+boys_status boys_eval_contract_f32(const float *x, int64_t count, int n_max, const float *c, int64_t c_row,
+                                   int64_t c_col, float *out, void *stream) {
+  if (count < 0) return BOYS_ERR_COUNT;
+  if (n_max < 0 || n_max > kMaxNF32) return BOYS_ERR_NMAX;
+  if (c_row < 0 || c_col < 0) return BOYS_ERR_ARG;
+  if (count == 0) return BOYS_OK;
+  if (!x || !c || !out) return BOYS_ERR_NULL;
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(out)) %
+      sizeof(float))
+    return BOYS_ERR_ALIGN;
+  int rc = device_ok();
+  if (rc) return (boys_status)rc;
+  if ((rc = device_accessible(x)) || (rc = device_accessible(c)) || (rc = device_accessible(out)))
+    return (boys_status)rc;
+  rc = boys_contract_f32_dispatch(n_max, x, count, c, c_row, c_col, out, static_cast<cudaStream_t>(stream));
+  return (boys_status)(rc < 0 ? BOYS_ERR_NMAX : rc);
 }
 
 size_t boys_eval_f64_host_workspace(int n_max, int64_t chunk) {

@@ -32,24 +32,54 @@ __device__ __forceinline__ bool below_cutoff_f32(float v, unsigned zbits) {
   return ((b >> 31) == 0 || mag == 0) && mag <= zbits;
 }
 
-template <int NMAX>
+// MODE 0 writes rows F_0..F_NMAX; MODE 1 is the fused contraction
+// out[i] = sum_m c[i, m] F_m(x_i) (one float per argument).
+template <int NMAX, int MODE = 0>
 struct F32Tile {
   static constexpr int W = NMAX + 1;
-  static constexpr int TILE = W <= 9 ? 1024 : 512;
+  static constexpr int WO = MODE == 0 ? W : 1;  // floats written per argument
+  static constexpr int TILE = W <= 9 || MODE == 1 ? 1024 : 512;
   static constexpr int BLOCK = 256;
-  // xs[TILE] floats, rows[TILE*W] floats, tab[64] floats, lst[TILE] u16
-  static constexpr size_t kSmem = sizeof(float) * (TILE + TILE * W + 64) + sizeof(unsigned short) * TILE;
+  // rows[TILE*WO] floats, xs[TILE] floats, tab[64] floats, lst[TILE] u16
+  static constexpr size_t kSmem = sizeof(float) * (TILE + TILE * WO + 64) + sizeof(unsigned short) * TILE;
 };
 
-template <int NMAX>
+struct F32Coef {
+  const float *c;  // contraction coefficients (MODE 1), element (i, m) at c[i*c_row + m*c_col]
+  int64_t c_row, c_col;
+};
+
+// cu: the coefficients held in registers when they are the same for every
+// argument (row stride 0), so the contraction costs no loads per argument
+template <int W, int MODE>
+__device__ __forceinline__ void f32_emit(float *__restrict__ rows, int j, int64_t i, const float (&F)[W],
+                                         const F32Coef &cf, const float (&cu)[W]) {
+  if constexpr (MODE == 0) {
+#pragma unroll
+    for (int m = 0; m < W; ++m) rows[j * W + m] = F[m];
+  } else {
+    float acc = 0.0f;
+    if (cf.c_row == 0) {
+#pragma unroll
+      for (int m = 0; m < W; ++m) acc = fmaf(cu[m], F[m], acc);
+    } else {
+      const float *ci = cf.c + i * cf.c_row;
+#pragma unroll
+      for (int m = 0; m < W; ++m) acc = fmaf(__ldg(ci + m * cf.c_col), F[m], acc);
+    }
+    rows[j] = acc;
+  }
+}
+
+template <int NMAX, int MODE>
 __global__ void __launch_bounds__(256) f32_split_kernel(const float *__restrict__ x, int64_t count,
-                                                        float *__restrict__ out) {
-  using P = F32Tile<NMAX>;
+                                                        float *__restrict__ out, const F32Coef cf) {
+  using P = F32Tile<NMAX, MODE>;
   constexpr int NTOP = f32_top_order(NMAX);
-  constexpr int W = P::W, TILE = P::TILE, BLOCK = P::BLOCK;
+  constexpr int W = P::W, WO = P::WO, TILE = P::TILE, BLOCK = P::BLOCK;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float *rows = reinterpret_cast<float *>(smem_raw);  // 16-byte aligned, TILE*W
-  float *xs = rows + TILE * W;
+  float *rows = reinterpret_cast<float *>(smem_raw);  // 16-byte aligned, TILE*WO
+  float *xs = rows + TILE * WO;
   float *tab = xs + TILE;
   unsigned short *lst = reinterpret_cast<unsigned short *>(tab + 64);
   __shared__ int cnt[1];
@@ -59,6 +89,9 @@ __global__ void __launch_bounds__(256) f32_split_kernel(const float *__restrict_
   const unsigned lt = (1u << lane) - 1u;
   const int64_t ntiles = (count + TILE - 1) / TILE;
   constexpr int PER = TILE / BLOCK;
+  float cu[W];
+#pragma unroll
+  for (int m = 0; m < W; ++m) cu[m] = (MODE == 1 && cf.c_row == 0) ? __ldg(cf.c + m * cf.c_col) : 0.0f;
   // the next tile's arguments are loaded into registers while the current
   // tile is evaluated, so the load latency hides behind the arithmetic
   float pre[PER];
@@ -85,12 +118,12 @@ __global__ void __launch_bounds__(256) f32_split_kernel(const float *__restrict_
     for (int k = 0; k < PER; ++k) {
       const int j = k * BLOCK + threadIdx.x;
       const float v = pre[k];
-      const bool lo = j < nel && below_cutoff_f32(v, zbits);
+      const bool valid = j < nel;
+      const bool lo = valid && below_cutoff_f32(v, zbits);
       xs[j] = v;
       float F[W];
       f32_asymptote<NMAX>(v, F);
-#pragma unroll
-      for (int m = 0; m < W; ++m) rows[j * W + m] = F[m];
+      if (MODE == 0 || valid) f32_emit<W, MODE>(rows, j, base + j, F, cf, cu);
       const unsigned mlo = __ballot_sync(0xffffffffu, lo);
       int plo = 0;
       if (lane == 0 && mlo) plo = atomicAdd(&cnt[0], __popc(mlo));
@@ -105,28 +138,27 @@ __global__ void __launch_bounds__(256) f32_split_kernel(const float *__restrict_
       const int j = lst[q];
       float F[W];
       f32_formula<NTOP, NMAX>(xs[j], F, tab);
-#pragma unroll
-      for (int m = 0; m < W; ++m) rows[j * W + m] = F[m];
+      f32_emit<W, MODE>(rows, j, base + j, F, cf, cu);
     }
-    float *dst = out + base * W;
-    const unsigned bytes = (unsigned)(nel * W * sizeof(float));
+    float *dst = out + base * WO;
+    const unsigned bytes = (unsigned)(nel * WO * sizeof(float));
     if (nel == TILE && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
       fence_proxy_async_smem();
       __syncthreads();
       if (threadIdx.x == 0) bulk_store_s2g(dst, rows, bytes);  // a full tile: 16-byte multiple
     } else {
       __syncthreads();
-      store_tile<float, BLOCK>(dst, rows, nel * W);
+      store_tile<float, BLOCK>(dst, rows, nel * WO);
       __syncthreads();
     }
   }
   if (threadIdx.x == 0) bulk_wait_all();
 }
 
-template <int NMAX>
-int launch_f32(const float *x, int64_t count, float *out, cudaStream_t s) {
-  using P = F32Tile<NMAX>;
-  auto k = f32_split_kernel<NMAX>;
+template <int NMAX, int MODE = 0>
+int launch_f32(const float *x, int64_t count, float *out, cudaStream_t s, F32Coef cf = F32Coef{nullptr, 0, 0}) {
+  using P = F32Tile<NMAX, MODE>;
+  auto k = f32_split_kernel<NMAX, MODE>;
   static int grid_cap = 0;
   if (grid_cap == 0) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::kSmem) != cudaSuccess)
@@ -135,7 +167,7 @@ int launch_f32(const float *x, int64_t count, float *out, cudaStream_t s) {
   }
   const int64_t tiles = (count + P::TILE - 1) / P::TILE;
   const int grid = (int)(tiles < grid_cap ? tiles : grid_cap);
-  k<<<grid, P::BLOCK, P::kSmem, s>>>(x, count, out);
+  k<<<grid, P::BLOCK, P::kSmem, s>>>(x, count, out, cf);
   return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
 }
 
@@ -144,3 +176,7 @@ int launch_f32(const float *x, int64_t count, float *out, cudaStream_t s) {
 #define BOYS_F32_CASE(k) \
   case k:                \
     return boys::launch_f32<k>(x, count, out, s);
+
+#define BOYS_F32_CONTRACT_CASE(k) \
+  case k:                         \
+    return boys::launch_f32<k, 1>(x, count, out, s, boys::F32Coef{c, c_row, c_col});

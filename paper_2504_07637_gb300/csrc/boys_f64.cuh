@@ -149,6 +149,22 @@ struct GradDot {
   }
 };
 
+// Contraction epilogue (a fused consumer): out[j] = sum_{m=0}^{W-1} c[j, m] F_m(x_j),
+// the rows never leave the registers.
+template <int W>
+struct ContractDot {
+  const double *c;  // row 0 of the tile
+  int64_t c_row, c_col;
+  double *out;  // element 0 of the tile
+  __device__ __forceinline__ void operator()(int j, const double (&F)[W]) const {
+    const double *cj = c + (int64_t)j * c_row;
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < W; ++m) acc = fma(__ldg(cj + m * c_col), F[m], acc);
+    out[j] = acc;
+  }
+};
+
 template <int TILE>
 struct F64TileSmem {
   double xs[TILE];
@@ -261,6 +277,16 @@ struct MakeGrad {
   }
 };
 
+template <int W>
+struct MakeContract {
+  const double *c;
+  int64_t c_row, c_col;
+  double *out;
+  __device__ __forceinline__ ContractDot<W> operator()(int64_t base) const {
+    return ContractDot<W>{c + base * c_row, c_row, c_col, out + base};
+  }
+};
+
 constexpr int kF64Block = 256, kF64Tile = 2048;
 
 template <int NMAX, typename MakeEpi>
@@ -286,7 +312,17 @@ int launch_f64_grad_recompute(const double *x, int64_t count, const double *g, i
   return launch_f64_epi<NMAX_FWD>(x, count, MakeGrad<NMAX_FWD + 1>{g, g_row, g_col, grad}, s);
 }
 
+template <int NMAX>
+int launch_f64_contract(const double *x, int64_t count, const double *c, int64_t c_row, int64_t c_col, double *out,
+                        cudaStream_t s) {
+  return launch_f64_epi<NMAX>(x, count, MakeContract<NMAX + 1>{c, c_row, c_col, out}, s);
+}
+
 }  // namespace boys
+
+#define BOYS_F64_CONTRACT_CASE(k) \
+  case k:                         \
+    return boys::launch_f64_contract<k>(x, count, c, c_row, c_col, out, s);
 
 #define BOYS_F64_CASE(k) \
   case k:                \

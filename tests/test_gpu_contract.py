@@ -1,0 +1,70 @@
+"""Fused consumer: out = sum_m c_m F_m(x) computed inside the evaluation
+kernel, against the oracle's rows contracted in long double.
+
+Error measure: |out - ref| / sum_m |c_m| F_m(x) (signed coefficients cancel),
+bounded by 2e-14 (FP64) and 2e-6 (FP32, where the terms are normal floats)."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_07637_gb300.build import build_library
+
+    build_library()
+    import paper_2504_07637_gb300 as boys
+
+    return boys
+
+
+def _ref(oracle_mod, x64, c, n_max):
+    F = oracle_mod.boys_ld(x64, n_max)
+    cl = np.broadcast_to(np.asarray(c, dtype=np.longdouble), F.shape)
+    return (cl * F).sum(axis=1).astype(np.float64), (np.abs(cl) * F).sum(axis=1).astype(np.float64)
+
+
+@pytest.mark.parametrize("n_max", [0, 5, 8, 16, 36])
+@pytest.mark.parametrize("dense", [False, True])
+def test_f64_against_oracle(lib, oracle_mod, n_max, dense):
+    import torch
+
+    rng = np.random.default_rng(n_max)
+    x = np.concatenate([np.exp(rng.uniform(math.log(1e-7), math.log(1e4), 7000)), [0.0, 1e-300, 1e8]])
+    c = rng.standard_normal((x.size, n_max + 1) if dense else n_max + 1)
+    got = lib.boys_contract(torch.from_numpy(x).cuda(), n_max, torch.from_numpy(c).cuda()).cpu().numpy()
+    want, scale = _ref(oracle_mod, x, c, n_max)
+    assert (np.abs(got - want) / scale).max() <= 2e-14
+
+
+@pytest.mark.parametrize("n_max", [0, 8, 16])
+def test_f32_against_oracle(lib, oracle_mod, n_max):
+    import torch
+
+    rng = np.random.default_rng(50 + n_max)
+    xf = np.exp(rng.uniform(math.log(1e-6), math.log(80.0), 9001)).astype(np.float32)  # normal-range values
+    c = rng.standard_normal(n_max + 1).astype(np.float32)
+    got = lib.boys_contract(torch.from_numpy(xf).cuda(), n_max, torch.from_numpy(c).cuda()).cpu().numpy()
+    want, scale = _ref(oracle_mod, xf.astype(np.float64), c.astype(np.float64), n_max)
+    assert (np.abs(got - want) / scale).max() <= 2e-6
+
+
+def test_matches_rows_then_dot(lib):
+    # the fused result equals contracting the stored rows (same kernel body)
+    import torch
+
+    from paper_2504_07637_gb300 import workloads
+
+    x = torch.from_numpy(workloads.scale(1 << 20, seed=5)).cuda()
+    c = torch.randn(9, dtype=torch.float64, device="cuda")
+    fused = lib.boys_contract(x, 8, c)
+    rows = lib.boys(x, 8)
+    ref = rows @ c
+    scale = rows @ c.abs()
+    assert ((fused - ref).abs() / scale).max().item() <= 1e-15
