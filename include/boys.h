@@ -106,6 +106,15 @@ boys_status boys_eval_f32(const float *x, int64_t count, int n_max, float *out, 
 boys_status boys_eval_backward_f64(const double *x, const double *F, int64_t ld_F, const double *g, int64_t g_row_stride,
                                    int64_t g_col_stride, int64_t count, int n_max, double *grad_x, void *stream);
 
+/* FP64 forward with the two-point evaluation of Sec. 3 (Trick B): besides the
+ * closed form at n_top (for m > n_bar), the closed form is also evaluated at
+ * the top order of n_bar = n_max / 2 (for m <= n_bar), sharing e^{-x}; each
+ * part has its own, shorter downward recursion.  The low orders come out
+ * more accurate (e.g. F_0 at n_max = 36: about 5e-15 instead of 1.3e-14),
+ * at the cost of a second closed form below the cut-off.  Arguments, layout
+ * and bound (2e-14 for every m) as boys_eval_f64; n_max < 2 is the plain path. */
+boys_status boys_eval_f64_two_point(const double *x, int64_t count, int n_max, double *out, void *stream);
+
 /* Fused consumer: out[i] = sum_{m=0}^{n_max} c[i*c_row + m*c_col] F_m(x_i).
  * Integral codes use the Boys values at once, as inputs of a contraction or a
  * recurrence (Sec. 1: they are the special functions of one- and two-electron

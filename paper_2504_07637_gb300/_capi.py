@@ -33,6 +33,7 @@ SIGNATURES = {
     "boys_top_order_f32": (c_int, [c_int]),
     "boys_eval_f32": (c_int, [vp, i64, c_int, vp, vp]),
     "boys_eval_backward_f64": (c_int, [vp, vp, i64, vp, i64, i64, i64, c_int, vp, vp]),
+    "boys_eval_f64_two_point": (c_int, [vp, i64, c_int, vp, vp]),
     "boys_eval_contract_f64": (c_int, [vp, i64, c_int, vp, i64, i64, vp, vp]),
     "boys_eval_contract_f32": (c_int, [vp, i64, c_int, vp, i64, i64, vp, vp]),
     "boys_eval_f64_host_workspace": (c_size, [c_int, i64]),

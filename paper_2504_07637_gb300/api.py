@@ -38,16 +38,20 @@ def top_order_f32(n_max: int) -> int:
     return _capi.load().boys_top_order_f32(n_max)
 
 
-def boys(x: torch.Tensor, n_max: int, out: torch.Tensor | None = None) -> torch.Tensor:
+def boys(x: torch.Tensor, n_max: int, out: torch.Tensor | None = None, two_point: bool = False) -> torch.Tensor:
     """F_0..F_{n_max} at every element of x: a [x.numel(), n_max+1] tensor of
-    x's dtype (float64: 2e-14 max relative error; float32: 2e-6)."""
+    x's dtype (float64: 2e-14 max relative error; float32: 2e-6).
+    two_point (float64): also evaluate the closed form at n_max/2 for more
+    accurate low orders (Trick B of Sec. 3)."""
     xf = _check_input(x, (torch.float64, torch.float32))
     n = xf.numel()
     if out is None:
         out = torch.empty((n, n_max + 1), dtype=xf.dtype, device=xf.device)
     elif out.shape != (n, n_max + 1) or out.dtype != xf.dtype or not out.is_contiguous() or out.device != xf.device:
         raise ValueError("out must be a contiguous [count, n_max+1] tensor of x's dtype on x's device")
-    fn = "boys_eval_f64" if xf.dtype == torch.float64 else "boys_eval_f32"
+    if two_point and xf.dtype != torch.float64:
+        raise TypeError("the two-point evaluation is a float64 path")
+    fn = ("boys_eval_f64_two_point" if two_point else "boys_eval_f64") if xf.dtype == torch.float64 else "boys_eval_f32"
     with torch.cuda.device(xf.device):
         _capi.call(fn, xf.data_ptr(), n, int(n_max), out.data_ptr(), _stream_ptr(xf.device))
     return out

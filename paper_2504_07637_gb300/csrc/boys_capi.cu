@@ -22,6 +22,8 @@ int boys_contract_dispatch_p1(int n_max, const double *x, int64_t count, const d
                               int64_t c_col, double *out, cudaStream_t s);
 int boys_contract_f32_dispatch(int n_max, const float *x, int64_t count, const float *c, int64_t c_row, int64_t c_col,
                                float *out, cudaStream_t s);
+int boys_two_point_dispatch_p0(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
+int boys_two_point_dispatch_p1(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
 int boys_grad_saved_launch(const double *F, int64_t ld_F, const double *g, int64_t g_row, int64_t g_col,
                            int64_t count, int n_max, double *grad, cudaStream_t s);
 int boys_f32_dispatch_p1(int n_max, const float *x, int64_t count, float *out, cudaStream_t s);
@@ -247,6 +249,16 @@ boys_status boys_eval_backward_f64(const double *x, const double *F, int64_t ld_
     if (rc < 0) rc = BOYS_ERR_NMAX;
   }
   return (boys_status)rc;
+}
+
+boys_status boys_eval_f64_two_point(const double *x, int64_t count, int n_max, double *out, void *stream) {
+  if (n_max < 2 && n_max >= 0) return boys_eval_f64(x, count, n_max, out, stream);  // nothing to split
+  int rc = check_rows(x, count, n_max, kMaxNF64, out, sizeof(double));
+  if (rc || count == 0) return (boys_status)rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = n_max <= 20 ? boys_two_point_dispatch_p0(n_max, x, count, out, s)
+                   : boys_two_point_dispatch_p1(n_max, x, count, out, s);
+  return (boys_status)(rc < 0 ? BOYS_ERR_NMAX : rc);
 }
 
 boys_status boys_eval_contract_f64(const double *x, int64_t count, int n_max, const double *c, int64_t c_row,

@@ -64,32 +64,59 @@ __device__ __forceinline__ double exp_neg(double x, const double *__restrict__ t
 //   F_NTOP = c_NTOP D^{-s}
 //   F_{m-1} = (2x F_m + e^{-x}) / (2m-1)     (Eq. "r", same e^{-x}; the printed
 //                                             denominator 2m+1 is read as 2m-1)
-template <int NTOP, int NMAX>
-__device__ __forceinline__ void f64_formula(const double x, double (&F)[NMAX + 1], const double *__restrict__ tab64) {
+// F_NTOP(x) by the closed form of Eq. "fq", given e = e^{-x}.
+template <int NTOP>
+__device__ __forceinline__ double f64_closed_form(const double x, const double e) {
   using Tab = BoysF64<NTOP>;
   double u, v;
   Tab::uv(x, u, v);
   const double r = u / v;
   const double p = (Tab::kQ2 * x) * x;
   const double q = fma(p, r, fma(Tab::kQ1, x, Tab::kQ0));
-  const double e = exp_neg(x, tab64);
   const double T = (ipow<NTOP>(q) * (q * rsqrt(q))) * e;
   const double D = x + T;
-  double f;
   if constexpr (NTOP <= 13) {
     const double rs = rsqrt(D);  // D^{-s} = rs^{2 NTOP + 1}
-    f = (Tab::kC * rs) * ipow<NTOP>(rs * rs);
+    return (Tab::kC * rs) * ipow<NTOP>(rs * rs);
   } else {
     const double w = 1.0 / D;  // D^{-s} = w^NTOP sqrt(w)
-    f = (Tab::kC * ipow<NTOP>(w)) * (w * rsqrt(w));
+    return (Tab::kC * ipow<NTOP>(w)) * (w * rsqrt(w));
   }
-  const double tx = twice(x);
+}
+
+// Downward recursion of Eq. "r" from F_TOP to F_LO, storing F_m for
+// LO <= m <= min(TOP, NMAX).
+template <int TOP, int LO, int NMAX>
+__device__ __forceinline__ void f64_recurse(double f, const double tx, const double e, double (&F)[NMAX + 1]) {
 #pragma unroll
-  for (int m = NTOP; m >= 1; --m) {
+  for (int m = TOP; m > LO; --m) {
     if (m <= NMAX) F[m] = f;
     f = fma(tx, f, e) * (1.0 / double(2 * m - 1));
   }
-  F[0] = f;
+  if (LO <= NMAX) F[LO] = f;
+}
+
+template <int NTOP, int NMAX>
+__device__ __forceinline__ void f64_formula(const double x, double (&F)[NMAX + 1], const double *__restrict__ tab64) {
+  const double e = exp_neg(x, tab64);
+  f64_recurse<NTOP, 0, NMAX>(f64_closed_form<NTOP>(x, e), twice(x), e, F);
+}
+
+// Two-point evaluation (Trick B of Sec. 3): the closed form at two orders,
+// NTOP for m > NBAR and NTOP_LO (>= NBAR) for m <= NBAR, with one recursion
+// each and one shared e^{-x}; the low orders then carry the error of a short
+// recursion from a low order instead of a long one from the top.
+template <int NTOP, int NTOP_LO, int NBAR, int NMAX>
+__device__ __forceinline__ void f64_formula_two(const double x, double (&F)[NMAX + 1],
+                                                const double *__restrict__ tab64) {
+  static_assert(NBAR < NMAX && NTOP_LO >= NBAR && NTOP_LO < NTOP, "orders");
+  const double e = exp_neg(x, tab64);
+  const double tx = twice(x);
+  f64_recurse<NTOP, NBAR + 1, NMAX>(f64_closed_form<NTOP>(x, e), tx, e, F);
+  double lo[NBAR + 1];
+  f64_recurse<NTOP_LO, 0, NBAR>(f64_closed_form<NTOP_LO>(x, e), tx, e, lo);
+#pragma unroll
+  for (int m = 0; m <= NBAR; ++m) F[m] = lo[m];
 }
 
 // Above the cut-off (or x negative, infinite or NaN): the asymptote of
@@ -176,7 +203,10 @@ struct F64TileSmem {
 // One tile of nel <= TILE arguments xt[0..nel): classify, build the two lists,
 // evaluate each list 32 entries per warp request and hand rows to epi.
 // All threads of the block call it; it begins and ends with a barrier.
-template <int NMAX, int BLOCK, int TILE, typename Epi>
+// Order n_bar of the two-point evaluation: the lower half of the orders.
+__host__ __device__ constexpr int f64_two_point_nbar(int n_max) { return n_max / 2; }
+
+template <int NMAX, int BLOCK, int TILE, typename Epi, bool TWO = false>
 __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel, const Epi &epi,
                                          F64TileSmem<TILE> &sm) {
   constexpr int NTOP = f64_top_order(NMAX);
@@ -221,7 +251,12 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
     if (q < nlo) {
       const int j = sm.lst[q];
       double F[W];
-      f64_formula<NTOP, NMAX>(sm.xs[j], F, sm.tab64);
+      if constexpr (TWO) {
+        constexpr int NBAR = f64_two_point_nbar(NMAX);
+        f64_formula_two<NTOP, f64_top_order(NBAR), NBAR, NMAX>(sm.xs[j], F, sm.tab64);
+      } else {
+        f64_formula<NTOP, NMAX>(sm.xs[j], F, sm.tab64);
+      }
       epi(j, F);
     }
   }
@@ -248,7 +283,7 @@ __device__ __forceinline__ void f64_load_table(F64TileSmem<TILE> &sm) {
 }
 
 // Plain and gradient kernels: persistent blocks stride over the tiles.
-template <int NMAX, int BLOCK, int TILE, typename MakeEpi>
+template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO = false>
 __global__ void __launch_bounds__(BLOCK) f64_split_kernel(const double *__restrict__ x, int64_t count,
                                                           const MakeEpi make) {
   __shared__ F64TileSmem<TILE> sm;
@@ -257,7 +292,7 @@ __global__ void __launch_bounds__(BLOCK) f64_split_kernel(const double *__restri
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t base = t * TILE;
     const int nel = (int)((count - base) < TILE ? (count - base) : TILE);
-    f64_tile<NMAX, BLOCK, TILE>(x + base, nel, make(base), sm);
+    f64_tile<NMAX, BLOCK, TILE, decltype(make(base)), TWO>(x + base, nel, make(base), sm);
   }
 }
 
@@ -289,9 +324,9 @@ struct MakeContract {
 
 constexpr int kF64Block = 256, kF64Tile = 2048;
 
-template <int NMAX, typename MakeEpi>
+template <int NMAX, typename MakeEpi, bool TWO = false>
 int launch_f64_epi(const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s) {
-  auto k = f64_split_kernel<NMAX, kF64Block, kF64Tile, MakeEpi>;
+  auto k = f64_split_kernel<NMAX, kF64Block, kF64Tile, MakeEpi, TWO>;
   static int grid_cap = 0;
   if (grid_cap == 0) grid_cap = persistent_grid(k, kF64Block, 0, INT64_MAX);
   const int64_t tiles = (count + kF64Tile - 1) / kF64Tile;
@@ -312,6 +347,12 @@ int launch_f64_grad_recompute(const double *x, int64_t count, const double *g, i
   return launch_f64_epi<NMAX_FWD>(x, count, MakeGrad<NMAX_FWD + 1>{g, g_row, g_col, grad}, s);
 }
 
+// Two-point evaluation (Trick B): rows as launch_f64.
+template <int NMAX>
+int launch_f64_two_point(const double *x, int64_t count, double *out, cudaStream_t s) {
+  return launch_f64_epi<NMAX, MakeStore<NMAX + 1>, true>(x, count, MakeStore<NMAX + 1>{out}, s);
+}
+
 template <int NMAX>
 int launch_f64_contract(const double *x, int64_t count, const double *c, int64_t c_row, int64_t c_col, double *out,
                         cudaStream_t s) {
@@ -319,6 +360,10 @@ int launch_f64_contract(const double *x, int64_t count, const double *c, int64_t
 }
 
 }  // namespace boys
+
+#define BOYS_F64_TWO_CASE(k) \
+  case k:                    \
+    return boys::launch_f64_two_point<k>(x, count, out, s);
 
 #define BOYS_F64_CONTRACT_CASE(k) \
   case k:                         \

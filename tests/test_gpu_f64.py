@@ -209,3 +209,30 @@ def test_host_pipeline_matches_device_path(lib, pinned):
     host_ws = torch.empty(ws_bytes + 256, dtype=torch.uint8)
     hp = host_ws.data_ptr() + (-host_ws.data_ptr()) % 256  # aligned, but host memory
     assert f(xh.data_ptr(), count, n_max, out.data_ptr(), hp, ws_bytes, s.cuda_stream) == 7
+
+
+@pytest.mark.parametrize("n_max", [2, 9, 16, 24, 36])
+def test_two_point_within_bound(lib, oracle_mod, n_max):
+    import torch
+
+    rng = np.random.default_rng(700 + n_max)
+    z = lib.cutoff(lib.top_order_f64(n_max), 53)
+    x = np.concatenate([np.exp(rng.uniform(math.log(1e-8), math.log(2 * z), 4000)), [0.0, 1e6, np.inf]])
+    got = lib.boys(torch.from_numpy(x).cuda(), n_max, two_point=True).cpu().numpy()
+    assert _relerr(got, oracle_mod.boys(x, n_max)).max() <= TOL
+
+
+def test_two_point_improves_low_orders(lib, oracle_mod):
+    # Trick B of Sec. 3: the low orders come from a short recursion
+    import torch
+
+    n_max = 36
+    z = lib.cutoff(lib.top_order_f64(n_max), 53)
+    x = np.linspace(1e-3, z, 40000)
+    ref = oracle_mod.boys(x, n_max)
+    xd = torch.from_numpy(x).cuda()
+    one = _relerr(lib.boys(xd, n_max).cpu().numpy(), ref)
+    two = _relerr(lib.boys(xd, n_max, two_point=True).cpu().numpy(), ref)
+    nbar = n_max // 2
+    assert two[:, : nbar + 1].max() < 0.7 * one[:, : nbar + 1].max(), (two[:, : nbar + 1].max(), one[:, : nbar + 1].max())
+    assert two.max() <= TOL
