@@ -31,6 +31,9 @@ WORKLOADS = {
     "scale_f64_n0": dict(count=1 << 26, n_max=0, dtype="f64"),
     "scale_f64_n4": dict(count=1 << 26, n_max=4, dtype="f64"),
     "scale_f64_n16": dict(count=1 << 26, n_max=16, dtype="f64"),
+    "scale_f64_n36": dict(count=1 << 24, n_max=36, dtype="f64"),
+    # two-point evaluation (Trick B): second closed form at n_max/2
+    "two_point_f64_n36": dict(count=1 << 24, n_max=36, dtype="f64", two_point=True),
     # the float path on the same arguments rounded to float
     "scale_f32_n8": dict(count=1 << 26, n_max=8, dtype="f32"),
     "scale_f32_n16": dict(count=1 << 26, n_max=16, dtype="f32"),
@@ -42,6 +45,8 @@ WORKLOADS = {
     "scale_f64_n8_small": dict(count=1 << 22, n_max=8, dtype="f64"),
     "scale_f32_n8_small": dict(count=1 << 24, n_max=8, dtype="f32"),
     "scale_f64_n16_small": dict(count=1 << 22, n_max=16, dtype="f64"),
+    "scale_f64_n36_small": dict(count=1 << 21, n_max=36, dtype="f64"),
+    "two_point_f64_n36_small": dict(count=1 << 21, n_max=36, dtype="f64", two_point=True),
     # fused consumer: sum_m w_m F_m(x) per argument, rows kept in registers
     "contract_f64_n8": dict(count=1 << 26, n_max=8, dtype="f64", kind="contract"),
     "contract_f32_n8": dict(count=1 << 26, n_max=8, dtype="f32", kind="contract"),
@@ -528,7 +533,7 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
     n_max, count = wl["n_max"], wl["count"]
     f32 = wl["dtype"] == "f32"
     np_t, th_t, esz = (np.float32, torch.float32, 4) if f32 else (np.float64, torch.float64, 8)
-    fn = "boys_eval_f32" if f32 else "boys_eval_f64"
+    fn = "boys_eval_f32" if f32 else ("boys_eval_f64_two_point" if wl.get("two_point") else "boys_eval_f64")
     x_host = workloads.scale(count, seed=seed).astype(np_t)
     x = torch.from_numpy(x_host).to(device)
     out = torch.empty((count, n_max + 1), dtype=th_t, device=device)
@@ -557,7 +562,7 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
     res = {"ms": ms, "values": count * (n_max + 1), "clocks": clk, "x_host": x_host}
     hbm_peak, hbm_src = measured_peaks()
     hbm_gbs = roofline.bytes_per_arg(n_max, esz) * count / (ms / 1e3) / 1e9
-    if not f32 and rates is not None:
+    if not f32 and rates is not None and not wl.get("two_point"):
         n_top = _capi.load().boys_top_order_f64(n_max)
         z = _capi.load().boys_cutoff(n_top, 53)
         fb = float(np.mean(x_host <= z))
@@ -737,11 +742,14 @@ def main():
     # the other configurations, summarised in the same line (single GPU, default run only)
     if ws == 1 and not args.no_extras and args.workload == "scale_f64_n8":
         suite = {"plain_f64_n8_65536": measure_plain(device, rates)}
-        for name in ("scale_f64_n0", "scale_f64_n4", "scale_f64_n16", "scale_f32_n8", "scale_f32_n16"):
+        for name in ("scale_f64_n0", "scale_f64_n4", "scale_f64_n16", "scale_f64_n36", "two_point_f64_n36",
+                     "scale_f32_n8", "scale_f32_n16"):
             r = measure_scale(WORKLOADS[name], 10, 3, device, seed, rates=rates)
             suite[name] = {"value": round(r["values"] / (r["ms"] / 1e3) / 1e9, 4), "unit": "G F_m values/s",
-                           "ms_per_step": round(r["ms"], 4), "roofline_bound": r["roofline"]["bound"],
-                           "roofline_frac": r["roofline"]["frac"]}
+                           "ms_per_step": round(r["ms"], 4)}
+            if "roofline" in r:
+                suite[name]["roofline_bound"] = r["roofline"]["bound"]
+                suite[name]["roofline_frac"] = r["roofline"]["frac"]
         for name in ("contract_f64_n8", "contract_f32_n8"):
             suite[name] = measure_contract(WORKLOADS[name], 10, 3, device, seed, rates=rates)
         sub = argparse.Namespace(steps=10, warmup=3, gpus=1)

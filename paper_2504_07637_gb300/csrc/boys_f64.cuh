@@ -241,13 +241,27 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
   }
   __syncthreads();
   const int nlo = sm.cnt[0], nhi = sm.cnt[1];
-  // closed form on the below-cut-off list, 32 entries per warp request
+  // closed form on the below-cut-off list, 32 entries per warp request; for
+  // high orders a lane takes two entries, whose long recursion chains then
+  // interleave (the FP64 result latency, not the pipe, would set the pace)
+  constexpr int ILP = (NMAX >= 12 && !TWO) ? 2 : 1;
   for (;;) {
     int c = 0;
-    if (lane == 0) c = atomicAdd(&sm.next[0], 32);
+    if (lane == 0) c = atomicAdd(&sm.next[0], 32 * ILP);
     c = __shfl_sync(0xffffffffu, c, 0);
     if (c >= nlo) break;
     const int q = c + lane;
+    if constexpr (ILP == 2) {
+      if (q + 32 < nlo) {
+        const int ja = sm.lst[q], jb = sm.lst[q + 32];
+        double Fa[W], Fb[W];
+        f64_formula<NTOP, NMAX>(sm.xs[ja], Fa, sm.tab64);
+        f64_formula<NTOP, NMAX>(sm.xs[jb], Fb, sm.tab64);
+        epi(ja, Fa);
+        epi(jb, Fb);
+        continue;
+      }
+    }
     if (q < nlo) {
       const int j = sm.lst[q];
       double F[W];
@@ -260,13 +274,25 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
       epi(j, F);
     }
   }
-  // asymptote on the above-cut-off list
+  // asymptote on the above-cut-off list (two entries per lane for high
+  // orders, as above: the upward product chain is 2 n_max long)
   for (;;) {
     int c = 0;
-    if (lane == 0) c = atomicAdd(&sm.next[1], 32);
+    if (lane == 0) c = atomicAdd(&sm.next[1], 32 * ILP);
     c = __shfl_sync(0xffffffffu, c, 0);
     if (c >= nhi) break;
     const int q = c + lane;
+    if constexpr (ILP == 2) {
+      if (q + 32 < nhi) {
+        const int ja = sm.lst[TILE - 1 - q], jb = sm.lst[TILE - 1 - (q + 32)];
+        double Fa[W], Fb[W];
+        f64_asymptote<NMAX>(sm.xs[ja], Fa);
+        f64_asymptote<NMAX>(sm.xs[jb], Fb);
+        epi(ja, Fa);
+        epi(jb, Fb);
+        continue;
+      }
+    }
     if (q < nhi) {
       const int j = sm.lst[TILE - 1 - q];
       double F[W];
