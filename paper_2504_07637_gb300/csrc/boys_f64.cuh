@@ -206,7 +206,9 @@ struct F64TileSmem {
 // Order n_bar of the two-point evaluation: the lower half of the orders.
 __host__ __device__ constexpr int f64_two_point_nbar(int n_max) { return n_max / 2; }
 
-template <int NMAX, int BLOCK, int TILE, typename Epi, bool TWO = false>
+// ALLOW_ILP = false keeps one list entry per lane at every order (a kernel
+// that switches between orders keeps the register count of the smallest).
+template <int NMAX, int BLOCK, int TILE, typename Epi, bool TWO = false, bool ALLOW_ILP = true>
 __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel, const Epi &epi,
                                          F64TileSmem<TILE> &sm) {
   constexpr int NTOP = f64_top_order(NMAX);
@@ -244,7 +246,7 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
   // closed form on the below-cut-off list, 32 entries per warp request; for
   // high orders a lane takes two entries, whose long recursion chains then
   // interleave (the FP64 result latency, not the pipe, would set the pace)
-  constexpr int ILP = (NMAX >= 12 && !TWO) ? 2 : 1;
+  constexpr int ILP = (NMAX >= 12 && !TWO && ALLOW_ILP) ? 2 : 1;
   for (;;) {
     int c = 0;
     if (lane == 0) c = atomicAdd(&sm.next[0], 32 * ILP);

@@ -114,7 +114,8 @@ __device__ __forceinline__ void ragged_tile(const RaggedArgs &a, int r, int64_t 
   const int64_t hi = a.offsets[r + 1];
   const int nel = (int)((hi - lo) < TILE ? (hi - lo) : TILE);
   double *rows = a.out + a.out_offsets[r] + (k * TILE) * (NMAX + 1);
-  boys::f64_tile<NMAX, BLOCK, TILE>(a.x + lo, nel, boys::StoreRows<NMAX + 1>{rows}, sm);
+  boys::f64_tile<NMAX, BLOCK, TILE, boys::StoreRows<NMAX + 1>, false, false>(a.x + lo, nel,
+                                                                             boys::StoreRows<NMAX + 1>{rows}, sm);
 }
 
 template <int BLOCK, int TILE>
