@@ -38,8 +38,11 @@ template <int NMAX, int MODE = 0>
 struct F32Tile {
   static constexpr int W = NMAX + 1;
   static constexpr int WO = MODE == 0 ? W : 1;  // floats written per argument
+  // 8 arguments per thread; small blocks keep the closed-form list's last
+  // round of a tile well filled (about 30% of a tile is listed, and a block
+  // waits for its slowest warp), measured best on GB300 for each band
   static constexpr int TILE = W <= 9 || MODE == 1 ? 1024 : 512;
-  static constexpr int BLOCK = 256;
+  static constexpr int BLOCK = W <= 9 || MODE == 1 ? 128 : 64;
   // rows[TILE*WO] floats, xs[TILE] floats, tab[64] floats, lst[TILE] u16
   static constexpr size_t kSmem = sizeof(float) * (TILE + TILE * WO + 64) + sizeof(unsigned short) * TILE;
 };
@@ -72,7 +75,7 @@ __device__ __forceinline__ void f32_emit(float *__restrict__ rows, int j, int64_
 }
 
 template <int NMAX, int MODE>
-__global__ void __launch_bounds__(256) f32_split_kernel(const float *__restrict__ x, int64_t count,
+__global__ void __launch_bounds__(F32Tile<NMAX, MODE>::BLOCK) f32_split_kernel(const float *__restrict__ x, int64_t count,
                                                         float *__restrict__ out, const F32Coef cf) {
   using P = F32Tile<NMAX, MODE>;
   constexpr int NTOP = f32_top_order(NMAX);
