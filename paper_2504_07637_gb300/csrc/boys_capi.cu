@@ -30,9 +30,9 @@ int boys_f32_dispatch_p1(int n_max, const float *x, int64_t count, float *out, c
 
 namespace {
 
+using boys::f32_top_order;
+using boys::kMaxNF32;
 using boys::kMaxNF64;
-constexpr int kMaxNF32 = 16;  // as in boys_f32.cuh
-constexpr int f32_top_order(int n_max) { return n_max <= 8 ? n_max : n_max + 1; }
 
 // The kernels are built for sm_103a only; reject other devices up front
 // instead of failing inside a launch.

@@ -40,6 +40,11 @@ __host__ __device__ constexpr int f64_top_order(int n_max) {
 }
 constexpr int kMaxNF64 = 36;
 
+// n_top for the float path: the closed form of order n_max itself up to 8,
+// one order higher above (Sec. 3's F_{n+1} trick) to keep F_{n_max} within 2e-6.
+__host__ __device__ constexpr int f32_top_order(int n_max) { return n_max <= 8 ? n_max : n_max + 1; }
+constexpr int kMaxNF32 = 16;
+
 // Persistent-grid size for a kernel: resident blocks per SM times SM count.
 template <typename Kernel>
 inline int persistent_grid(Kernel k, int block, size_t smem, int64_t tiles) {

@@ -19,10 +19,6 @@ namespace boys {
 
 static __constant__ float kExp2Frac32ff[64] = BOYS_EXP2_FRAC32_FF;
 
-// n_top for the float path: the closed form of order n_max itself up to 8,
-// one order higher above (Sec. 3's F_{n+1} trick) to keep F_{n_max} within 2e-6.
-__host__ __device__ constexpr int f32_top_order(int n_max) { return n_max <= 8 ? n_max : n_max + 1; }
-constexpr int kMaxNF32 = 16;
 static_assert(f32_top_order(kMaxNF32) <= BOYS_F32_TABLE_MAX_N, "fitted table too short");
 
 // +-0 and 0 < x <= z by the bit pattern (negative nonzero and NaN excluded)
