@@ -37,12 +37,17 @@ using boys::kMaxNF64;
 // The kernels are built for sm_103a only; reject other devices up front
 // instead of failing inside a launch.
 int device_ok() {
+  // the answer per device never changes: 0 unknown, 1 sm_103, 2 other
+  static unsigned char known[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return BOYS_ERR_CUDA;
+  if (dev >= 0 && dev < 64 && known[dev]) return known[dev] == 1 ? BOYS_OK : BOYS_ERR_DEVICE;
   int major = 0, minor = 0;
   if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return BOYS_ERR_CUDA;
   if (cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) return BOYS_ERR_CUDA;
-  return (major == 10 && minor == 3) ? BOYS_OK : BOYS_ERR_DEVICE;
+  const bool ok = major == 10 && minor == 3;
+  if (dev >= 0 && dev < 64) known[dev] = ok ? 1 : 2;
+  return ok ? BOYS_OK : BOYS_ERR_DEVICE;
 }
 
 // A pointer the GPU cannot dereference (plain pageable host memory) would
