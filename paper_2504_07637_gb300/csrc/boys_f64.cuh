@@ -352,15 +352,28 @@ struct MakeContract {
 
 constexpr int kF64Block = 256, kF64Tile = 2048;
 
+// Below this many arguments the work would not fill the GPU with 2048-argument
+// tiles (a 65,536-argument call is 32 tiles for 152 SMs), so small tiles are
+// used: the per-argument arithmetic, and so every result, is the same.
+constexpr int64_t kF64SmallCount = 1 << 20;
+constexpr int kF64SmallBlock = 128, kF64SmallTile = 256;
+
+template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO>
+int launch_f64_shape(const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s) {
+  auto k = f64_split_kernel<NMAX, BLOCK, TILE, MakeEpi, TWO>;
+  static int grid_cap = 0;
+  if (grid_cap == 0) grid_cap = persistent_grid(k, BLOCK, 0, INT64_MAX);
+  const int64_t tiles = (count + TILE - 1) / TILE;
+  const int grid = (int)(tiles < grid_cap ? tiles : grid_cap);
+  k<<<grid, BLOCK, 0, s>>>(x, count, epi);
+  return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
+}
+
 template <int NMAX, typename MakeEpi, bool TWO = false>
 int launch_f64_epi(const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s) {
-  auto k = f64_split_kernel<NMAX, kF64Block, kF64Tile, MakeEpi, TWO>;
-  static int grid_cap = 0;
-  if (grid_cap == 0) grid_cap = persistent_grid(k, kF64Block, 0, INT64_MAX);
-  const int64_t tiles = (count + kF64Tile - 1) / kF64Tile;
-  const int grid = (int)(tiles < grid_cap ? tiles : grid_cap);
-  k<<<grid, kF64Block, 0, s>>>(x, count, epi);
-  return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
+  if (count <= kF64SmallCount)
+    return launch_f64_shape<NMAX, kF64SmallBlock, kF64SmallTile, MakeEpi, TWO>(x, count, epi, s);
+  return launch_f64_shape<NMAX, kF64Block, kF64Tile, MakeEpi, TWO>(x, count, epi, s);
 }
 
 template <int NMAX>

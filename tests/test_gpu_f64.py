@@ -236,3 +236,17 @@ def test_two_point_improves_low_orders(lib, oracle_mod):
     nbar = n_max // 2
     assert two[:, : nbar + 1].max() < 0.7 * one[:, : nbar + 1].max(), (two[:, : nbar + 1].max(), one[:, : nbar + 1].max())
     assert two.max() <= TOL
+
+
+@pytest.mark.parametrize("n_max", [0, 8, 16])
+def test_small_and_large_launch_shapes_agree_bitwise(lib, n_max):
+    # calls below 2^20 arguments use small tiles; the arithmetic per argument,
+    # and so every bit of the result, must be the same as with large tiles
+    import torch
+
+    from paper_2504_07637_gb300 import workloads
+
+    x = torch.from_numpy(workloads.scale((1 << 21) + 77, seed=n_max)).cuda()
+    big = lib.boys(x, n_max)
+    parts = [lib.boys(x[i:i + (1 << 19)], n_max) for i in range(0, x.numel(), 1 << 19)]
+    assert torch.equal(big, torch.cat(parts))
