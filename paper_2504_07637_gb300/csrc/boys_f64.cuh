@@ -169,15 +169,10 @@ struct GradDot {
   double *grad;  // element 0 of the tile
   __device__ __forceinline__ void operator()(int j, const double (&F)[W]) const {
     const double *gj = g + (int64_t)j * g_row;
-    // even and odd terms in two accumulators, in the same order as the
-    // saved-rows backward kernel (so both give the same bits)
-    double acc0 = 0.0, acc1 = 0.0;
+    double acc = 0.0;
 #pragma unroll
-    for (int m = 0; m + 1 < W; m += 2) {
-      acc0 = fma(__ldg(gj + m * g_col), F[m + 1], acc0);
-      if (m + 2 < W) acc1 = fma(__ldg(gj + (m + 1) * g_col), F[m + 2], acc1);
-    }
-    grad[j] = -(acc0 + acc1);
+    for (int m = 0; m + 1 < W; ++m) acc = fma(__ldg(gj + m * g_col), F[m + 1], acc);
+    grad[j] = -acc;
   }
 };
 
