@@ -14,17 +14,10 @@ __global__ void __launch_bounds__(256) grad_saved_kernel(const double *__restric
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     const double *Fi = F + i * ld_F + 1;
     const double *gi = g + i * g_row;
-    // two accumulators: the FP64 result latency would otherwise pace one
-    // chain of n_max+1 dependent fused multiply-adds
-    double acc0 = 0.0, acc1 = 0.0;
-    int m = 0;
+    double acc = 0.0;
 #pragma unroll 4
-    for (; m + 1 < terms; m += 2) {
-      acc0 = fma(__ldg(gi + m * g_col), __ldg(Fi + m), acc0);
-      acc1 = fma(__ldg(gi + (m + 1) * g_col), __ldg(Fi + m + 1), acc1);
-    }
-    if (m < terms) acc0 = fma(__ldg(gi + m * g_col), __ldg(Fi + m), acc0);
-    grad[i] = -(acc0 + acc1);
+    for (int m = 0; m < terms; ++m) acc = fma(__ldg(gi + m * g_col), __ldg(Fi + m), acc);
+    grad[i] = -acc;
   }
 }
 
