@@ -138,6 +138,51 @@ __device__ __forceinline__ void f64_asymptote(const double x, double (&F)[NMAX +
   }
 }
 
+// The same arithmetic as f64_formula / f64_asymptote for K arguments at once
+// (K = 1 or 2), with each F_m written to its row as soon as it exists: no row
+// is held in registers, and the K dependent chains interleave step by step.
+template <int NTOP, int NMAX, int K>
+__device__ __forceinline__ void f64_formula_stream(const double (&x)[K], double *const (&dst)[K],
+                                                   const double *__restrict__ tab64) {
+  double e[K], tx[K], f[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    e[k] = exp_neg(x[k], tab64);
+    tx[k] = twice(x[k]);
+    f[k] = f64_closed_form<NTOP>(x[k], e[k]);
+  }
+#pragma unroll
+  for (int m = NTOP; m > 0; --m) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (m <= NMAX) __stcs(dst[k] + m, f[k]);
+      f[k] = fma(tx[k], f[k], e[k]) * (1.0 / double(2 * m - 1));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) __stcs(dst[k], f[k]);
+}
+
+template <int NMAX, int K>
+__device__ __forceinline__ void f64_asymptote_stream(const double (&x)[K], double *const (&dst)[K]) {
+  double f[K], y[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double rs = rsqrt(x[k]);
+    f[k] = 0.88622692545275801365 * rs;
+    __stcs(dst[k], f[k]);
+    if constexpr (NMAX >= 1) y[k] = NMAX <= 12 ? rs * rs : 1.0 / x[k];
+  }
+#pragma unroll
+  for (int m = 1; m <= NMAX; ++m) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      f[k] = f[k] * ((double(m) - 0.5) * y[k]);
+      __stcs(dst[k] + m, f[k]);
+    }
+  }
+}
+
 template <int W>
 __device__ __forceinline__ void store_row(double *__restrict__ dst, const double (&F)[W]) {
 #pragma unroll
@@ -156,14 +201,17 @@ __device__ __forceinline__ bool below_cutoff(double v, unsigned long long zbits)
 // of the current tile (j counts from the tile's first argument).
 template <int W>
 struct StoreRows {
+  static constexpr bool kStream = true;  // rows may be written one F_m at a time
   double *out;  // row 0 of the tile
   __device__ __forceinline__ void operator()(int j, const double (&F)[W]) const { store_row<W>(out + (int64_t)j * W, F); }
+  __device__ __forceinline__ double *row(int j) const { return out + (int64_t)j * W; }
 };
 
 // Gradient epilogue: grad[j] = -sum_{m=0}^{W-2} g[j, m] F_{m+1}(x_j)
 // (dF_m/dx = -F_{m+1}, from differentiating Eq. "fn" under the integral).
 template <int W>
 struct GradDot {
+  static constexpr bool kStream = false;  // sums in a fixed order over the whole row
   const double *g;  // row 0 of the tile
   int64_t g_row, g_col;
   double *grad;  // element 0 of the tile
@@ -180,6 +228,7 @@ struct GradDot {
 // the rows never leave the registers.
 template <int W>
 struct ContractDot {
+  static constexpr bool kStream = false;
   const double *c;  // row 0 of the tile
   int64_t c_row, c_col;
   double *out;  // element 0 of the tile
@@ -247,6 +296,10 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
   // high orders a lane takes two entries, whose long recursion chains then
   // interleave (the FP64 result latency, not the pipe, would set the pace)
   constexpr int ILP = (NMAX >= 12 && !TWO && ALLOW_ILP) ? 2 : 1;
+  // with two entries per lane a store epilogue takes F_m as the recursion
+  // makes it: two whole rows in registers would halve the resident warps
+  // (one entry per lane keeps its row: there that uses fewer registers)
+  constexpr bool STREAM = Epi::kStream && ILP == 2;
   for (;;) {
     int c = 0;
     if (lane == 0) c = atomicAdd(&sm.next[0], 32 * ILP);
@@ -256,16 +309,28 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
     if constexpr (ILP == 2) {
       if (q + 32 < nlo) {
         const int ja = sm.lst[q], jb = sm.lst[q + 32];
-        double Fa[W], Fb[W];
-        f64_formula<NTOP, NMAX>(sm.xs[ja], Fa, sm.tab64);
-        f64_formula<NTOP, NMAX>(sm.xs[jb], Fb, sm.tab64);
-        epi(ja, Fa);
-        epi(jb, Fb);
+        if constexpr (STREAM) {
+          const double xv[2] = {sm.xs[ja], sm.xs[jb]};
+          double *const d[2] = {epi.row(ja), epi.row(jb)};
+          f64_formula_stream<NTOP, NMAX, 2>(xv, d, sm.tab64);
+        } else {
+          double Fa[W], Fb[W];
+          f64_formula<NTOP, NMAX>(sm.xs[ja], Fa, sm.tab64);
+          f64_formula<NTOP, NMAX>(sm.xs[jb], Fb, sm.tab64);
+          epi(ja, Fa);
+          epi(jb, Fb);
+        }
         continue;
       }
     }
     if (q < nlo) {
       const int j = sm.lst[q];
+      if constexpr (STREAM) {
+        const double xv[1] = {sm.xs[j]};
+        double *const d[1] = {epi.row(j)};
+        f64_formula_stream<NTOP, NMAX, 1>(xv, d, sm.tab64);
+        continue;
+      }
       double F[W];
       if constexpr (TWO) {
         constexpr int NBAR = f64_two_point_nbar(NMAX);
@@ -287,16 +352,28 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
     if constexpr (ILP == 2) {
       if (q + 32 < nhi) {
         const int ja = sm.lst[TILE - 1 - q], jb = sm.lst[TILE - 1 - (q + 32)];
-        double Fa[W], Fb[W];
-        f64_asymptote<NMAX>(sm.xs[ja], Fa);
-        f64_asymptote<NMAX>(sm.xs[jb], Fb);
-        epi(ja, Fa);
-        epi(jb, Fb);
+        if constexpr (STREAM) {
+          const double xv[2] = {sm.xs[ja], sm.xs[jb]};
+          double *const d[2] = {epi.row(ja), epi.row(jb)};
+          f64_asymptote_stream<NMAX, 2>(xv, d);
+        } else {
+          double Fa[W], Fb[W];
+          f64_asymptote<NMAX>(sm.xs[ja], Fa);
+          f64_asymptote<NMAX>(sm.xs[jb], Fb);
+          epi(ja, Fa);
+          epi(jb, Fb);
+        }
         continue;
       }
     }
     if (q < nhi) {
       const int j = sm.lst[TILE - 1 - q];
+      if constexpr (STREAM) {
+        const double xv[1] = {sm.xs[j]};
+        double *const d[1] = {epi.row(j)};
+        f64_asymptote_stream<NMAX, 1>(xv, d);
+        continue;
+      }
       double F[W];
       f64_asymptote<NMAX>(sm.xs[j], F);
       epi(j, F);

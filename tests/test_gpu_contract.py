@@ -68,3 +68,23 @@ def test_matches_rows_then_dot(lib):
     ref = rows @ c
     scale = rows @ c.abs()
     assert ((fused - ref).abs() / scale).max().item() <= 1e-15
+
+
+@pytest.mark.parametrize("n_max", [12, 23, 36])
+@pytest.mark.parametrize("count", [5000, (1 << 20) + 3001])
+def test_one_hot_contraction_equals_rows_bitwise(lib, n_max, count):
+    # The contraction keeps each row in registers, the row store at n_max >= 12
+    # writes F_m as the recursion makes it: with c = e_m the contraction adds
+    # exact zeros to F_m, so both paths must give the same bits (small and
+    # large launch shapes, both lists of a tile, ragged tails).
+    import torch
+
+    from paper_2504_07637_gb300 import workloads
+
+    x = torch.from_numpy(np.concatenate([workloads.scale(count - 3, seed=n_max), [0.0, 1e-300, 1e8]])).cuda()
+    rows = lib.boys(x, n_max)
+    for m in (0, n_max // 2, n_max):
+        c = torch.zeros(n_max + 1, dtype=torch.float64, device="cuda")
+        c[m] = 1.0
+        got = lib.boys_contract(x, n_max, c)
+        assert torch.equal(got, rows[:, m]), m
