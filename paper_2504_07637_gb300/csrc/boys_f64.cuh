@@ -20,6 +20,8 @@
 #include "boys_coeffs_f64.inc"
 #include "boys_common.cuh"
 
+#include <type_traits>
+
 namespace boys {
 
 // 2^(j/64), j = 0..63, for the exponential below
@@ -183,6 +185,100 @@ __device__ __forceinline__ void f64_asymptote_stream(const double (&x)[K], doubl
   }
 }
 
+// Compile-time loop: f(std::integral_constant<int, I>) for I = BEGIN, BEGIN + STEP, ... up to END (excluded).
+template <int I, int END, int STEP, typename Fn>
+__device__ __forceinline__ void static_for(Fn &&f) {
+  if constexpr ((STEP > 0 && I < END) || (STEP < 0 && I > END)) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + STEP, END, STEP>(f);
+  }
+}
+
+// Staged row stores for a warp that holds 64 rows (two list entries per
+// lane).  A row store of F_m from 32 lanes touches 32 sectors (the rows are
+// W doubles apart), so the warp first collects F_m for CH consecutive m of
+// its 64 rows in shared memory (row pitch CH + 1, odd: conflict-free 64-bit
+// lane access) and then writes the 64 x LEN block with consecutive lanes on
+// consecutive elements of a row, about 11 sectors per store at CH = 8.
+template <int CH>
+struct F64Stage {
+  static constexpr int kPitch = CH + 1;
+  static constexpr int kDoublesPerWarp = 64 * kPitch;
+};
+
+// Write columns m0 .. m0 + LEN - 1 of the warp's 64 staged rows: row r < 32
+// belongs to list entry a of lane r, row 32 + r to entry b of lane r.
+// The row index comes from a volatile shuffle: the addresses of a flush are
+// the same for every chunk but m0, and kept live across the recursion they
+// would cost two registers per store.
+__device__ __forceinline__ int shfl_idx_volatile(int v, int src) {
+  int r;
+  asm volatile("shfl.sync.idx.b32 %0, %1, %2, 0x1f, 0xffffffff;" : "=r"(r) : "r"(v), "r"(src));
+  return r;
+}
+
+template <int W, int CH, int LEN>
+__device__ __forceinline__ void f64_stage_flush(double *__restrict__ out, double *__restrict__ stg, int m0, int ja,
+                                                int jb, int lane) {
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < 2 * LEN; ++t) {
+    const int f = 32 * t + lane;
+    const int r = f / LEN, e = f - r * LEN;
+    const int j = shfl_idx_volatile(t < LEN ? ja : jb, r & 31);
+    __stcs(out + ((int64_t)j * W + (m0 + e)), stg[r * F64Stage<CH>::kPitch + e]);
+  }
+  __syncwarp();
+}
+
+// f64_formula for list entries a (row ja) and b (row jb) of every lane of a
+// full warp, rows staged as above; the arithmetic is f64_formula's.
+template <int NTOP, int NMAX, int CH>
+__device__ __forceinline__ void f64_formula_pair_staged(const double xa, const double xb, const int ja, const int jb,
+                                                        double *__restrict__ out, double *__restrict__ stg,
+                                                        const double *__restrict__ tab64, const int lane) {
+  constexpr int W = NMAX + 1;
+  const double ea = exp_neg(xa, tab64), eb = exp_neg(xb, tab64);
+  const double ta = twice(xa), tb = twice(xb);
+  double fa = f64_closed_form<NTOP>(xa, ea), fb = f64_closed_form<NTOP>(xb, eb);
+  double *sa = stg + lane * F64Stage<CH>::kPitch, *sb = stg + (32 + lane) * F64Stage<CH>::kPitch;
+  static_for<NTOP, -1, -1>([&](auto mc) {
+    constexpr int m = decltype(mc)::value;
+    if constexpr (m <= NMAX) {
+      sa[m % CH] = fa;
+      sb[m % CH] = fb;
+      if constexpr (m % CH == 0) f64_stage_flush<W, CH, (W - m < CH ? W - m : CH)>(out, stg, m, ja, jb, lane);
+    }
+    if constexpr (m > 0) {
+      fa = fma(ta, fa, ea) * (1.0 / double(2 * m - 1));
+      fb = fma(tb, fb, eb) * (1.0 / double(2 * m - 1));
+    }
+  });
+}
+
+// f64_asymptote for entries a and b of every lane of a full warp, staged.
+template <int NMAX, int CH>
+__device__ __forceinline__ void f64_asymptote_pair_staged(const double xa, const double xb, const int ja, const int jb,
+                                                          double *__restrict__ out, double *__restrict__ stg,
+                                                          const int lane) {
+  constexpr int W = NMAX + 1;
+  const double ra = rsqrt(xa), rb = rsqrt(xb);
+  double fa = 0.88622692545275801365 * ra, fb = 0.88622692545275801365 * rb;
+  const double ya = NMAX <= 12 ? ra * ra : 1.0 / xa, yb = NMAX <= 12 ? rb * rb : 1.0 / xb;
+  double *sa = stg + lane * F64Stage<CH>::kPitch, *sb = stg + (32 + lane) * F64Stage<CH>::kPitch;
+  static_for<0, W, 1>([&](auto mc) {
+    constexpr int m = decltype(mc)::value;
+    if constexpr (m > 0) {
+      fa = fa * ((double(m) - 0.5) * ya);
+      fb = fb * ((double(m) - 0.5) * yb);
+    }
+    sa[m % CH] = fa;
+    sb[m % CH] = fb;
+    if constexpr (m % CH == CH - 1 || m == NMAX)
+      f64_stage_flush<W, CH, m % CH + 1>(out, stg, m - m % CH, ja, jb, lane);
+  });
+}
+
 template <int W>
 __device__ __forceinline__ void store_row(double *__restrict__ dst, const double (&F)[W]) {
 #pragma unroll
@@ -257,9 +353,9 @@ __host__ __device__ constexpr int f64_two_point_nbar(int n_max) { return n_max /
 
 // ALLOW_ILP = false keeps one list entry per lane at every order (a kernel
 // that switches between orders keeps the register count of the smallest).
-template <int NMAX, int BLOCK, int TILE, typename Epi, bool TWO = false, bool ALLOW_ILP = true>
+template <int NMAX, int BLOCK, int TILE, typename Epi, bool TWO = false, bool ALLOW_ILP = true, int STAGE = 0>
 __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel, const Epi &epi,
-                                         F64TileSmem<TILE> &sm) {
+                                         F64TileSmem<TILE> &sm, double *__restrict__ stage = nullptr) {
   constexpr int NTOP = f64_top_order(NMAX);
   constexpr int W = NMAX + 1;
   static_assert(TILE % BLOCK == 0 && TILE <= 65536, "tile");
@@ -296,41 +392,44 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
   // high orders a lane takes two entries, whose long recursion chains then
   // interleave (the FP64 result latency, not the pipe, would set the pace)
   constexpr int ILP = (NMAX >= 12 && !TWO && ALLOW_ILP) ? 2 : 1;
-  // with two entries per lane a store epilogue takes F_m as the recursion
-  // makes it: two whole rows in registers would halve the resident warps
-  // (one entry per lane keeps its row: there that uses fewer registers)
-  constexpr bool STREAM = Epi::kStream && ILP == 2;
+  // rows of a store epilogue with two entries per lane go out through the
+  // warp's staging buffer (STAGE orders at a time); a request with fewer than
+  // 64 entries left (the last of a list) stores its rows one F_m at a time
+  constexpr bool STAGED = STAGE > 0 && ILP == 2 && Epi::kStream;
+  double *const stg = STAGED ? stage + (threadIdx.x >> 5) * F64Stage<(STAGE > 0 ? STAGE : 1)>::kDoublesPerWarp : nullptr;
   for (;;) {
     int c = 0;
     if (lane == 0) c = atomicAdd(&sm.next[0], 32 * ILP);
     c = __shfl_sync(0xffffffffu, c, 0);
     if (c >= nlo) break;
     const int q = c + lane;
+    if constexpr (STAGED) {
+      if (c + 64 <= nlo) {  // the whole warp: entries q and q + 32
+        const int ja = sm.lst[q], jb = sm.lst[q + 32];
+        f64_formula_pair_staged<NTOP, NMAX, STAGE>(sm.xs[ja], sm.xs[jb], ja, jb, epi.out, stg, sm.tab64, lane);
+      } else {
+        for (int qq = q; qq < nlo && qq < c + 64; qq += 32) {
+          const int j = sm.lst[qq];
+          const double xv[1] = {sm.xs[j]};
+          double *const d[1] = {epi.row(j)};
+          f64_formula_stream<NTOP, NMAX, 1>(xv, d, sm.tab64);
+        }
+      }
+      continue;
+    }
     if constexpr (ILP == 2) {
       if (q + 32 < nlo) {
         const int ja = sm.lst[q], jb = sm.lst[q + 32];
-        if constexpr (STREAM) {
-          const double xv[2] = {sm.xs[ja], sm.xs[jb]};
-          double *const d[2] = {epi.row(ja), epi.row(jb)};
-          f64_formula_stream<NTOP, NMAX, 2>(xv, d, sm.tab64);
-        } else {
-          double Fa[W], Fb[W];
-          f64_formula<NTOP, NMAX>(sm.xs[ja], Fa, sm.tab64);
-          f64_formula<NTOP, NMAX>(sm.xs[jb], Fb, sm.tab64);
-          epi(ja, Fa);
-          epi(jb, Fb);
-        }
+        double Fa[W], Fb[W];
+        f64_formula<NTOP, NMAX>(sm.xs[ja], Fa, sm.tab64);
+        f64_formula<NTOP, NMAX>(sm.xs[jb], Fb, sm.tab64);
+        epi(ja, Fa);
+        epi(jb, Fb);
         continue;
       }
     }
     if (q < nlo) {
       const int j = sm.lst[q];
-      if constexpr (STREAM) {
-        const double xv[1] = {sm.xs[j]};
-        double *const d[1] = {epi.row(j)};
-        f64_formula_stream<NTOP, NMAX, 1>(xv, d, sm.tab64);
-        continue;
-      }
       double F[W];
       if constexpr (TWO) {
         constexpr int NBAR = f64_two_point_nbar(NMAX);
@@ -349,31 +448,33 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
     c = __shfl_sync(0xffffffffu, c, 0);
     if (c >= nhi) break;
     const int q = c + lane;
+    if constexpr (STAGED) {
+      if (c + 64 <= nhi) {
+        const int ja = sm.lst[TILE - 1 - q], jb = sm.lst[TILE - 1 - (q + 32)];
+        f64_asymptote_pair_staged<NMAX, STAGE>(sm.xs[ja], sm.xs[jb], ja, jb, epi.out, stg, lane);
+      } else {
+        for (int qq = q; qq < nhi && qq < c + 64; qq += 32) {
+          const int j = sm.lst[TILE - 1 - qq];
+          const double xv[1] = {sm.xs[j]};
+          double *const d[1] = {epi.row(j)};
+          f64_asymptote_stream<NMAX, 1>(xv, d);
+        }
+      }
+      continue;
+    }
     if constexpr (ILP == 2) {
       if (q + 32 < nhi) {
         const int ja = sm.lst[TILE - 1 - q], jb = sm.lst[TILE - 1 - (q + 32)];
-        if constexpr (STREAM) {
-          const double xv[2] = {sm.xs[ja], sm.xs[jb]};
-          double *const d[2] = {epi.row(ja), epi.row(jb)};
-          f64_asymptote_stream<NMAX, 2>(xv, d);
-        } else {
-          double Fa[W], Fb[W];
-          f64_asymptote<NMAX>(sm.xs[ja], Fa);
-          f64_asymptote<NMAX>(sm.xs[jb], Fb);
-          epi(ja, Fa);
-          epi(jb, Fb);
-        }
+        double Fa[W], Fb[W];
+        f64_asymptote<NMAX>(sm.xs[ja], Fa);
+        f64_asymptote<NMAX>(sm.xs[jb], Fb);
+        epi(ja, Fa);
+        epi(jb, Fb);
         continue;
       }
     }
     if (q < nhi) {
       const int j = sm.lst[TILE - 1 - q];
-      if constexpr (STREAM) {
-        const double xv[1] = {sm.xs[j]};
-        double *const d[1] = {epi.row(j)};
-        f64_asymptote_stream<NMAX, 1>(xv, d);
-        continue;
-      }
       double F[W];
       f64_asymptote<NMAX>(sm.xs[j], F);
       epi(j, F);
@@ -387,18 +488,51 @@ __device__ __forceinline__ void f64_load_table(F64TileSmem<TILE> &sm) {
   for (int i = threadIdx.x; i < 64; i += BLOCK) sm.tab64[i] = kExp2Frac64[i];
 }
 
-// Plain and gradient kernels: persistent blocks stride over the tiles.
-template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO = false>
-__global__ void __launch_bounds__(BLOCK) f64_split_kernel(const double *__restrict__ x, int64_t count,
-                                                          const MakeEpi make) {
-  __shared__ F64TileSmem<TILE> sm;
+template <int BLOCK, int STAGE>
+constexpr size_t f64_stage_bytes() {
+  return STAGE > 0 ? sizeof(double) * (BLOCK / 32) * F64Stage<(STAGE > 0 ? STAGE : 1)>::kDoublesPerWarp : 0;
+}
+
+// Resident blocks per SM that a staged kernel is compiled for: as many as its
+// shared memory allows (228 KB per SM, 1 KB reserved per block), at most 4;
+// the register budget follows from it.
+template <int BLOCK, int TILE, int STAGE>
+constexpr int f64_min_blocks() {
+  if (STAGE == 0) return 1;
+  const size_t per_block = sizeof(F64TileSmem<TILE>) + f64_stage_bytes<BLOCK, STAGE>() + 1024;
+  const int b = (int)((size_t)228 * 1024 / per_block);
+  return b < 1 ? 1 : (b > 4 ? 4 : b);
+}
+
+// Tiles of a persistent block (all kernels below).
+template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO, int STAGE>
+__device__ __forceinline__ void f64_tiles(const double *__restrict__ x, int64_t count, const MakeEpi &make,
+                                          F64TileSmem<TILE> &sm, double *__restrict__ stage) {
   f64_load_table<BLOCK, TILE>(sm);
   const int64_t ntiles = (count + TILE - 1) / TILE;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t base = t * TILE;
     const int nel = (int)((count - base) < TILE ? (count - base) : TILE);
-    f64_tile<NMAX, BLOCK, TILE, decltype(make(base)), TWO>(x + base, nel, make(base), sm);
+    f64_tile<NMAX, BLOCK, TILE, decltype(make(base)), TWO, true, STAGE>(x + base, nel, make(base), sm, stage);
   }
+}
+
+// Plain, gradient and contraction kernels: persistent blocks stride over the tiles.
+template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO = false>
+__global__ void __launch_bounds__(BLOCK) f64_split_kernel(const double *__restrict__ x, int64_t count,
+                                                          const MakeEpi make) {
+  __shared__ F64TileSmem<TILE> sm;
+  f64_tiles<NMAX, BLOCK, TILE, MakeEpi, TWO, 0>(x, count, make, sm, nullptr);
+}
+
+// Rows with two list entries per lane, staged (dynamic shared memory of
+// f64_stage_bytes), compiled for f64_min_blocks resident blocks.
+template <int NMAX, int BLOCK, int TILE, typename MakeEpi, int STAGE>
+__global__ void __launch_bounds__(BLOCK, (f64_min_blocks<BLOCK, TILE, STAGE>()))
+    f64_staged_kernel(const double *__restrict__ x, int64_t count, const MakeEpi make) {
+  __shared__ F64TileSmem<TILE> sm;
+  extern __shared__ __align__(16) unsigned char f64_stage_raw[];
+  f64_tiles<NMAX, BLOCK, TILE, MakeEpi, false, STAGE>(x, count, make, sm, reinterpret_cast<double *>(f64_stage_raw));
 }
 
 template <int W>
@@ -435,27 +569,50 @@ constexpr int kF64Block = 256, kF64Tile = 2048;
 constexpr int64_t kF64SmallCount = 1 << 20;
 constexpr int kF64SmallBlock = 128, kF64SmallTile = 256;
 
-template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO>
-int launch_f64_shape(const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s) {
-  auto k = f64_split_kernel<NMAX, BLOCK, TILE, MakeEpi, TWO>;
-  static int grid_cap = 0;
-  if (grid_cap == 0) grid_cap = persistent_grid(k, BLOCK, 0, INT64_MAX);
-  const int64_t tiles = (count + TILE - 1) / TILE;
+// Launch kernel k on a persistent grid (grid_cap: its resident blocks, found
+// on the first call).
+template <typename Kernel, typename MakeEpi>
+int launch_f64_persistent(Kernel k, int &grid_cap, int block, int tile, size_t dyn, const double *x, int64_t count,
+                          const MakeEpi &epi, cudaStream_t s) {
+  if (grid_cap == 0) {
+    if (dyn > 0 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+      return BOYS_ERR_CUDA;
+    grid_cap = persistent_grid(k, block, dyn, INT64_MAX);
+  }
+  const int64_t tiles = (count + tile - 1) / tile;
   const int grid = (int)(tiles < grid_cap ? tiles : grid_cap);
-  k<<<grid, BLOCK, 0, s>>>(x, count, epi);
+  k<<<grid, block, dyn, s>>>(x, count, epi);
   return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
 }
 
-template <int NMAX, typename MakeEpi, bool TWO = false>
+template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO, int STAGE = 0>
+int launch_f64_shape(const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s) {
+  static int grid_cap = 0;
+  if constexpr (STAGE > 0) {
+    static_assert(!TWO, "staging serves the one-point rows");
+    return launch_f64_persistent(f64_staged_kernel<NMAX, BLOCK, TILE, MakeEpi, STAGE>, grid_cap, BLOCK, TILE,
+                                 f64_stage_bytes<BLOCK, STAGE>(), x, count, epi, s);
+  } else {
+    return launch_f64_persistent(f64_split_kernel<NMAX, BLOCK, TILE, MakeEpi, TWO>, grid_cap, BLOCK, TILE, 0, x,
+                                 count, epi, s);
+  }
+}
+
+template <int NMAX, typename MakeEpi, bool TWO = false, int STAGE = 0>
 int launch_f64_epi(const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s) {
   if (count <= kF64SmallCount)
-    return launch_f64_shape<NMAX, kF64SmallBlock, kF64SmallTile, MakeEpi, TWO>(x, count, epi, s);
-  return launch_f64_shape<NMAX, kF64Block, kF64Tile, MakeEpi, TWO>(x, count, epi, s);
+    return launch_f64_shape<NMAX, kF64SmallBlock, kF64SmallTile, MakeEpi, TWO, STAGE>(x, count, epi, s);
+  return launch_f64_shape<NMAX, kF64Block, kF64Tile, MakeEpi, TWO, STAGE>(x, count, epi, s);
 }
+
+// Orders staged per flush of the row-staging buffer (rows of n_max >= 12,
+// where lanes take two list entries).
+constexpr int kF64StageOrders = 8;
 
 template <int NMAX>
 int launch_f64(const double *x, int64_t count, double *out, cudaStream_t s) {
-  return launch_f64_epi<NMAX>(x, count, MakeStore<NMAX + 1>{out}, s);
+  return launch_f64_epi<NMAX, MakeStore<NMAX + 1>, false, (NMAX >= 12 ? kF64StageOrders : 0)>(
+      x, count, MakeStore<NMAX + 1>{out}, s);
 }
 
 // Backward with the forward rows recomputed: the order n_max + 1 is needed.
