@@ -104,6 +104,9 @@ __device__ __forceinline__ void f64_formula(const double x, double (&F)[NMAX + 1
   f64_recurse<NTOP, 0, NMAX>(f64_closed_form<NTOP>(x, e), twice(x), e, F);
 }
 
+// Order n_bar of the two-point evaluation: the lower half of the orders.
+__host__ __device__ constexpr int f64_two_point_nbar(int n_max) { return n_max / 2; }
+
 // Two-point evaluation (Trick B of Sec. 3): the closed form at two orders,
 // NTOP for m > NBAR and NTOP_LO (>= NBAR) for m <= NBAR, with one recursion
 // each and one shared e^{-x}; the low orders then carry the error of a short
@@ -140,51 +143,6 @@ __device__ __forceinline__ void f64_asymptote(const double x, double (&F)[NMAX +
   }
 }
 
-// The same arithmetic as f64_formula / f64_asymptote for K arguments at once
-// (K = 1 or 2), with each F_m written to its row as soon as it exists: no row
-// is held in registers, and the K dependent chains interleave step by step.
-template <int NTOP, int NMAX, int K>
-__device__ __forceinline__ void f64_formula_stream(const double (&x)[K], double *const (&dst)[K],
-                                                   const double *__restrict__ tab64) {
-  double e[K], tx[K], f[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    e[k] = exp_neg(x[k], tab64);
-    tx[k] = twice(x[k]);
-    f[k] = f64_closed_form<NTOP>(x[k], e[k]);
-  }
-#pragma unroll
-  for (int m = NTOP; m > 0; --m) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (m <= NMAX) __stcs(dst[k] + m, f[k]);
-      f[k] = fma(tx[k], f[k], e[k]) * (1.0 / double(2 * m - 1));
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < K; ++k) __stcs(dst[k], f[k]);
-}
-
-template <int NMAX, int K>
-__device__ __forceinline__ void f64_asymptote_stream(const double (&x)[K], double *const (&dst)[K]) {
-  double f[K], y[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const double rs = rsqrt(x[k]);
-    f[k] = 0.88622692545275801365 * rs;
-    __stcs(dst[k], f[k]);
-    if constexpr (NMAX >= 1) y[k] = NMAX <= 12 ? rs * rs : 1.0 / x[k];
-  }
-#pragma unroll
-  for (int m = 1; m <= NMAX; ++m) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      f[k] = f[k] * ((double(m) - 0.5) * y[k]);
-      __stcs(dst[k] + m, f[k]);
-    }
-  }
-}
-
 // Compile-time loop: f(std::integral_constant<int, I>) for I = BEGIN, BEGIN + STEP, ... up to END (excluded).
 template <int I, int END, int STEP, typename Fn>
 __device__ __forceinline__ void static_for(Fn &&f) {
@@ -194,20 +152,18 @@ __device__ __forceinline__ void static_for(Fn &&f) {
   }
 }
 
-// Staged row stores for a warp that holds 64 rows (two list entries per
-// lane).  A row store of F_m from 32 lanes touches 32 sectors (the rows are
-// W doubles apart), so the warp first collects F_m for CH consecutive m of
-// its 64 rows in shared memory (row pitch CH + 1, odd: conflict-free 64-bit
-// lane access) and then writes the 64 x LEN block with consecutive lanes on
-// consecutive elements of a row, about 11 sectors per store at CH = 8.
-template <int CH>
+// Staged row stores.  A warp whose lanes hold K list entries each (32 K
+// rows) would store F_m from 32 lanes into 32 sectors (the rows are n_max+1
+// doubles apart).  Instead it collects F_m for CH consecutive m of its rows in
+// shared memory (odd row pitch: conflict-free 64-bit lane access) and writes
+// each 32K x LEN block with consecutive lanes on consecutive elements of a
+// row, about 11 sectors per store at CH = 8.
+template <int CH, int K>
 struct F64Stage {
-  static constexpr int kPitch = CH + 1;
-  static constexpr int kDoublesPerWarp = 64 * kPitch;
+  static constexpr int kPitch = CH | 1;
+  static constexpr int kDoublesPerWarp = 32 * K * kPitch;
 };
 
-// Write columns m0 .. m0 + LEN - 1 of the warp's 64 staged rows: row r < 32
-// belongs to list entry a of lane r, row 32 + r to entry b of lane r.
 // The row index comes from a volatile shuffle: the addresses of a flush are
 // the same for every chunk but m0, and kept live across the recursion they
 // would cost two registers per store.
@@ -217,65 +173,93 @@ __device__ __forceinline__ int shfl_idx_volatile(int v, int src) {
   return r;
 }
 
-template <int W, int CH, int LEN>
-__device__ __forceinline__ void f64_stage_flush(double *__restrict__ out, double *__restrict__ stg, int m0, int ja,
-                                                int jb, int lane) {
+// Write columns m0 .. m0 + LEN - 1 of the warp's staged rows: row 32 k + l
+// is entry k (row index j[k]) of lane l; j[k] < 0 marks a lane without one.
+template <int W, int CH, int K, int LEN>
+__device__ __forceinline__ void f64_stage_flush(double *__restrict__ out, const double *__restrict__ stg, int m0,
+                                                const int (&j)[K], int lane) {
   __syncwarp();
 #pragma unroll
-  for (int t = 0; t < 2 * LEN; ++t) {
+  for (int t = 0; t < K * LEN; ++t) {
     const int f = 32 * t + lane;
     const int r = f / LEN, e = f - r * LEN;
-    const int j = shfl_idx_volatile(t < LEN ? ja : jb, r & 31);
-    __stcs(out + ((int64_t)j * W + (m0 + e)), stg[r * F64Stage<CH>::kPitch + e]);
+    const int jr = shfl_idx_volatile(j[t / LEN], r & 31);
+    if (jr >= 0) __stcs(out + ((int64_t)jr * W + (m0 + e)), stg[r * F64Stage<CH, K>::kPitch + e]);
   }
   __syncwarp();
 }
 
-// f64_formula for list entries a (row ja) and b (row jb) of every lane of a
-// full warp, rows staged as above; the arithmetic is f64_formula's.
-template <int NTOP, int NMAX, int CH>
-__device__ __forceinline__ void f64_formula_pair_staged(const double xa, const double xb, const int ja, const int jb,
-                                                        double *__restrict__ out, double *__restrict__ stg,
-                                                        const double *__restrict__ tab64, const int lane) {
-  constexpr int W = NMAX + 1;
-  const double ea = exp_neg(xa, tab64), eb = exp_neg(xb, tab64);
-  const double ta = twice(xa), tb = twice(xb);
-  double fa = f64_closed_form<NTOP>(xa, ea), fb = f64_closed_form<NTOP>(xb, eb);
-  double *sa = stg + lane * F64Stage<CH>::kPitch, *sb = stg + (32 + lane) * F64Stage<CH>::kPitch;
-  static_for<NTOP, -1, -1>([&](auto mc) {
+// Downward recursion of Eq. "r" from F_TOP (in f) to F_LO, staging F_m for
+// LO <= m <= HI and flushing every chunk of CH orders whose lowest order is
+// reached (orders above HI of that chunk were staged before, by the other
+// recursion of a two-point evaluation).  The arithmetic is f64_recurse's.
+template <int TOP, int LO, int HI, int W, int CH, int K>
+__device__ __forceinline__ void f64_recurse_staged(double (&f)[K], const double (&tx)[K], const double (&e)[K],
+                                                   const int (&j)[K], double *__restrict__ out,
+                                                   double *__restrict__ stg, const int lane) {
+  static_for<TOP, LO - 1, -1>([&](auto mc) {
     constexpr int m = decltype(mc)::value;
-    if constexpr (m <= NMAX) {
-      sa[m % CH] = fa;
-      sb[m % CH] = fb;
-      if constexpr (m % CH == 0) f64_stage_flush<W, CH, (W - m < CH ? W - m : CH)>(out, stg, m, ja, jb, lane);
+    if constexpr (m <= HI) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + m % CH] = f[k];
+      if constexpr (m % CH == 0) f64_stage_flush<W, CH, K, (W - m < CH ? W - m : CH)>(out, stg, m, j, lane);
     }
-    if constexpr (m > 0) {
-      fa = fma(ta, fa, ea) * (1.0 / double(2 * m - 1));
-      fb = fma(tb, fb, eb) * (1.0 / double(2 * m - 1));
+    if constexpr (m > LO) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) f[k] = fma(tx[k], f[k], e[k]) * (1.0 / double(2 * m - 1));
     }
   });
 }
 
-// f64_asymptote for entries a and b of every lane of a full warp, staged.
-template <int NMAX, int CH>
-__device__ __forceinline__ void f64_asymptote_pair_staged(const double xa, const double xb, const int ja, const int jb,
-                                                          double *__restrict__ out, double *__restrict__ stg,
-                                                          const int lane) {
+// f64_formula (TWO = false) or f64_formula_two (TWO = true) for the K
+// entries of every lane of a full warp (rows j[k] of the tile), rows staged
+// as above; the arithmetic is theirs.
+template <int NTOP, int NMAX, int CH, int K, bool TWO>
+__device__ __forceinline__ void f64_formula_staged(const double (&x)[K], const int (&j)[K], double *__restrict__ out,
+                                                   double *__restrict__ stg, const double *__restrict__ tab64,
+                                                   const int lane) {
   constexpr int W = NMAX + 1;
-  const double ra = rsqrt(xa), rb = rsqrt(xb);
-  double fa = 0.88622692545275801365 * ra, fb = 0.88622692545275801365 * rb;
-  const double ya = NMAX <= 12 ? ra * ra : 1.0 / xa, yb = NMAX <= 12 ? rb * rb : 1.0 / xb;
-  double *sa = stg + lane * F64Stage<CH>::kPitch, *sb = stg + (32 + lane) * F64Stage<CH>::kPitch;
+  double e[K], tx[K], f[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    e[k] = exp_neg(x[k], tab64);
+    tx[k] = twice(x[k]);
+    f[k] = f64_closed_form<NTOP>(x[k], e[k]);
+  }
+  if constexpr (!TWO) {
+    f64_recurse_staged<NTOP, 0, NMAX, W, CH, K>(f, tx, e, j, out, stg, lane);
+  } else {
+    constexpr int NBAR = f64_two_point_nbar(NMAX);
+    constexpr int NTOP_LO = f64_top_order(NBAR);
+    static_assert(NBAR < NMAX && NTOP_LO >= NBAR && NTOP_LO < NTOP, "orders");
+    f64_recurse_staged<NTOP, NBAR + 1, NMAX, W, CH, K>(f, tx, e, j, out, stg, lane);
+#pragma unroll
+    for (int k = 0; k < K; ++k) f[k] = f64_closed_form<NTOP_LO>(x[k], e[k]);
+    f64_recurse_staged<NTOP_LO, 0, NBAR, W, CH, K>(f, tx, e, j, out, stg, lane);
+  }
+}
+
+// f64_asymptote for the K entries of every lane of a full warp, staged.
+template <int NMAX, int CH, int K>
+__device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const int (&j)[K],
+                                                     double *__restrict__ out, double *__restrict__ stg,
+                                                     const int lane) {
+  constexpr int W = NMAX + 1;
+  double f[K], y[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double rs = rsqrt(x[k]);
+    f[k] = 0.88622692545275801365 * rs;
+    y[k] = NMAX <= 12 ? rs * rs : 1.0 / x[k];
+  }
   static_for<0, W, 1>([&](auto mc) {
     constexpr int m = decltype(mc)::value;
-    if constexpr (m > 0) {
-      fa = fa * ((double(m) - 0.5) * ya);
-      fb = fb * ((double(m) - 0.5) * yb);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if constexpr (m > 0) f[k] = f[k] * ((double(m) - 0.5) * y[k]);
+      stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + m % CH] = f[k];
     }
-    sa[m % CH] = fa;
-    sb[m % CH] = fb;
-    if constexpr (m % CH == CH - 1 || m == NMAX)
-      f64_stage_flush<W, CH, m % CH + 1>(out, stg, m - m % CH, ja, jb, lane);
+    if constexpr (m % CH == CH - 1 || m == NMAX) f64_stage_flush<W, CH, K, m % CH + 1>(out, stg, m - m % CH, j, lane);
   });
 }
 
@@ -297,17 +281,16 @@ __device__ __forceinline__ bool below_cutoff(double v, unsigned long long zbits)
 // of the current tile (j counts from the tile's first argument).
 template <int W>
 struct StoreRows {
-  static constexpr bool kStream = true;  // rows may be written one F_m at a time
+  static constexpr bool kRowStore = true;  // the rows may go out through the staging buffer
   double *out;  // row 0 of the tile
   __device__ __forceinline__ void operator()(int j, const double (&F)[W]) const { store_row<W>(out + (int64_t)j * W, F); }
-  __device__ __forceinline__ double *row(int j) const { return out + (int64_t)j * W; }
 };
 
 // Gradient epilogue: grad[j] = -sum_{m=0}^{W-2} g[j, m] F_{m+1}(x_j)
 // (dF_m/dx = -F_{m+1}, from differentiating Eq. "fn" under the integral).
 template <int W>
 struct GradDot {
-  static constexpr bool kStream = false;  // sums in a fixed order over the whole row
+  static constexpr bool kRowStore = false;
   const double *g;  // row 0 of the tile
   int64_t g_row, g_col;
   double *grad;  // element 0 of the tile
@@ -324,7 +307,7 @@ struct GradDot {
 // the rows never leave the registers.
 template <int W>
 struct ContractDot {
-  static constexpr bool kStream = false;
+  static constexpr bool kRowStore = false;
   const double *c;  // row 0 of the tile
   int64_t c_row, c_col;
   double *out;  // element 0 of the tile
@@ -348,12 +331,11 @@ struct F64TileSmem {
 // One tile of nel <= TILE arguments xt[0..nel): classify, build the two lists,
 // evaluate each list 32 entries per warp request and hand rows to epi.
 // All threads of the block call it; it begins and ends with a barrier.
-// Order n_bar of the two-point evaluation: the lower half of the orders.
-__host__ __device__ constexpr int f64_two_point_nbar(int n_max) { return n_max / 2; }
 
 // ALLOW_ILP = false keeps one list entry per lane at every order (a kernel
 // that switches between orders keeps the register count of the smallest).
-template <int NMAX, int BLOCK, int TILE, typename Epi, bool TWO = false, bool ALLOW_ILP = true, int STAGE = 0>
+template <int NMAX, int BLOCK, int TILE, typename Epi, bool TWO = false, bool ALLOW_ILP = true, int STAGE = 0,
+          int STAGE_K = 2>
 __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel, const Epi &epi,
                                          F64TileSmem<TILE> &sm, double *__restrict__ stage = nullptr) {
   constexpr int NTOP = f64_top_order(NMAX);
@@ -391,12 +373,13 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
   // closed form on the below-cut-off list, 32 entries per warp request; for
   // high orders a lane takes two entries, whose long recursion chains then
   // interleave (the FP64 result latency, not the pipe, would set the pace)
-  constexpr int ILP = (NMAX >= 12 && !TWO && ALLOW_ILP) ? 2 : 1;
-  // rows of a store epilogue with two entries per lane go out through the
-  // warp's staging buffer (STAGE orders at a time); a request with fewer than
-  // 64 entries left (the last of a list) stores its rows one F_m at a time
-  constexpr bool STAGED = STAGE > 0 && ILP == 2 && Epi::kStream;
-  double *const stg = STAGED ? stage + (threadIdx.x >> 5) * F64Stage<(STAGE > 0 ? STAGE : 1)>::kDoublesPerWarp : nullptr;
+  // Staged rows (STAGE > 0, a store epilogue): STAGE_K entries per lane, the
+  // rows go out through the warp's staging buffer STAGE orders at a time.
+  constexpr bool STAGED = STAGE > 0;
+  static_assert(!STAGED || Epi::kRowStore, "staging serves row stores");
+  constexpr int ILP = STAGED ? STAGE_K : ((NMAX >= 12 && !TWO && ALLOW_ILP) ? 2 : 1);
+  using Stage = F64Stage<(STAGED ? STAGE : 1), ILP>;
+  double *const stg = STAGED ? stage + (threadIdx.x >> 5) * Stage::kDoublesPerWarp : nullptr;
   for (;;) {
     int c = 0;
     if (lane == 0) c = atomicAdd(&sm.next[0], 32 * ILP);
@@ -404,17 +387,16 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
     if (c >= nlo) break;
     const int q = c + lane;
     if constexpr (STAGED) {
-      if (c + 64 <= nlo) {  // the whole warp: entries q and q + 32
-        const int ja = sm.lst[q], jb = sm.lst[q + 32];
-        f64_formula_pair_staged<NTOP, NMAX, STAGE>(sm.xs[ja], sm.xs[jb], ja, jb, epi.out, stg, sm.tab64, lane);
-      } else {
-        for (int qq = q; qq < nlo && qq < c + 64; qq += 32) {
-          const int j = sm.lst[qq];
-          const double xv[1] = {sm.xs[j]};
-          double *const d[1] = {epi.row(j)};
-          f64_formula_stream<NTOP, NMAX, 1>(xv, d, sm.tab64);
-        }
+      // the whole warp takes part; lanes past the end of the list compute a
+      // dummy argument and store nothing
+      int j[ILP];
+      double xv[ILP];
+#pragma unroll
+      for (int k = 0; k < ILP; ++k) {
+        j[k] = q + 32 * k < nlo ? (int)sm.lst[q + 32 * k] : -1;
+        xv[k] = j[k] >= 0 ? sm.xs[j[k]] : 1.0;
       }
+      f64_formula_staged<NTOP, NMAX, STAGE, ILP, TWO>(xv, j, epi.out, stg, sm.tab64, lane);
       continue;
     }
     if constexpr (ILP == 2) {
@@ -449,17 +431,14 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
     if (c >= nhi) break;
     const int q = c + lane;
     if constexpr (STAGED) {
-      if (c + 64 <= nhi) {
-        const int ja = sm.lst[TILE - 1 - q], jb = sm.lst[TILE - 1 - (q + 32)];
-        f64_asymptote_pair_staged<NMAX, STAGE>(sm.xs[ja], sm.xs[jb], ja, jb, epi.out, stg, lane);
-      } else {
-        for (int qq = q; qq < nhi && qq < c + 64; qq += 32) {
-          const int j = sm.lst[TILE - 1 - qq];
-          const double xv[1] = {sm.xs[j]};
-          double *const d[1] = {epi.row(j)};
-          f64_asymptote_stream<NMAX, 1>(xv, d);
-        }
+      int j[ILP];
+      double xv[ILP];
+#pragma unroll
+      for (int k = 0; k < ILP; ++k) {
+        j[k] = q + 32 * k < nhi ? (int)sm.lst[TILE - 1 - (q + 32 * k)] : -1;
+        xv[k] = j[k] >= 0 ? sm.xs[j[k]] : 1.0;
       }
+      f64_asymptote_staged<NMAX, STAGE, ILP>(xv, j, epi.out, stg, lane);
       continue;
     }
     if constexpr (ILP == 2) {
@@ -488,24 +467,24 @@ __device__ __forceinline__ void f64_load_table(F64TileSmem<TILE> &sm) {
   for (int i = threadIdx.x; i < 64; i += BLOCK) sm.tab64[i] = kExp2Frac64[i];
 }
 
-template <int BLOCK, int STAGE>
+template <int BLOCK, int STAGE, int K>
 constexpr size_t f64_stage_bytes() {
-  return STAGE > 0 ? sizeof(double) * (BLOCK / 32) * F64Stage<(STAGE > 0 ? STAGE : 1)>::kDoublesPerWarp : 0;
+  return STAGE > 0 ? sizeof(double) * (BLOCK / 32) * F64Stage<(STAGE > 0 ? STAGE : 1), K>::kDoublesPerWarp : 0;
 }
 
 // Resident blocks per SM that a staged kernel is compiled for: as many as its
 // shared memory allows (228 KB per SM, 1 KB reserved per block), at most 4;
 // the register budget follows from it.
-template <int BLOCK, int TILE, int STAGE>
+template <int BLOCK, int TILE, int STAGE, int K>
 constexpr int f64_min_blocks() {
   if (STAGE == 0) return 1;
-  const size_t per_block = sizeof(F64TileSmem<TILE>) + f64_stage_bytes<BLOCK, STAGE>() + 1024;
+  const size_t per_block = sizeof(F64TileSmem<TILE>) + f64_stage_bytes<BLOCK, STAGE, K>() + 1024;
   const int b = (int)((size_t)228 * 1024 / per_block);
   return b < 1 ? 1 : (b > 4 ? 4 : b);
 }
 
 // Tiles of a persistent block (all kernels below).
-template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO, int STAGE>
+template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO, int STAGE, int K>
 __device__ __forceinline__ void f64_tiles(const double *__restrict__ x, int64_t count, const MakeEpi &make,
                                           F64TileSmem<TILE> &sm, double *__restrict__ stage) {
   f64_load_table<BLOCK, TILE>(sm);
@@ -513,7 +492,7 @@ __device__ __forceinline__ void f64_tiles(const double *__restrict__ x, int64_t 
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t base = t * TILE;
     const int nel = (int)((count - base) < TILE ? (count - base) : TILE);
-    f64_tile<NMAX, BLOCK, TILE, decltype(make(base)), TWO, true, STAGE>(x + base, nel, make(base), sm, stage);
+    f64_tile<NMAX, BLOCK, TILE, decltype(make(base)), TWO, true, STAGE, K>(x + base, nel, make(base), sm, stage);
   }
 }
 
@@ -522,17 +501,18 @@ template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO = false>
 __global__ void __launch_bounds__(BLOCK) f64_split_kernel(const double *__restrict__ x, int64_t count,
                                                           const MakeEpi make) {
   __shared__ F64TileSmem<TILE> sm;
-  f64_tiles<NMAX, BLOCK, TILE, MakeEpi, TWO, 0>(x, count, make, sm, nullptr);
+  f64_tiles<NMAX, BLOCK, TILE, MakeEpi, TWO, 0, 1>(x, count, make, sm, nullptr);
 }
 
-// Rows with two list entries per lane, staged (dynamic shared memory of
+// Staged rows, K list entries per lane (dynamic shared memory of
 // f64_stage_bytes), compiled for f64_min_blocks resident blocks.
-template <int NMAX, int BLOCK, int TILE, typename MakeEpi, int STAGE>
-__global__ void __launch_bounds__(BLOCK, (f64_min_blocks<BLOCK, TILE, STAGE>()))
+template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO, int STAGE, int K>
+__global__ void __launch_bounds__(BLOCK, (f64_min_blocks<BLOCK, TILE, STAGE, K>()))
     f64_staged_kernel(const double *__restrict__ x, int64_t count, const MakeEpi make) {
   __shared__ F64TileSmem<TILE> sm;
   extern __shared__ __align__(16) unsigned char f64_stage_raw[];
-  f64_tiles<NMAX, BLOCK, TILE, MakeEpi, false, STAGE>(x, count, make, sm, reinterpret_cast<double *>(f64_stage_raw));
+  f64_tiles<NMAX, BLOCK, TILE, MakeEpi, TWO, STAGE, K>(x, count, make, sm,
+                                                       reinterpret_cast<double *>(f64_stage_raw));
 }
 
 template <int W>
@@ -585,24 +565,23 @@ int launch_f64_persistent(Kernel k, int &grid_cap, int block, int tile, size_t d
   return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
 }
 
-template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO, int STAGE = 0>
+template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO, int STAGE = 0, int K = 2>
 int launch_f64_shape(const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s) {
   static int grid_cap = 0;
   if constexpr (STAGE > 0) {
-    static_assert(!TWO, "staging serves the one-point rows");
-    return launch_f64_persistent(f64_staged_kernel<NMAX, BLOCK, TILE, MakeEpi, STAGE>, grid_cap, BLOCK, TILE,
-                                 f64_stage_bytes<BLOCK, STAGE>(), x, count, epi, s);
+    return launch_f64_persistent(f64_staged_kernel<NMAX, BLOCK, TILE, MakeEpi, TWO, STAGE, K>, grid_cap, BLOCK, TILE,
+                                 f64_stage_bytes<BLOCK, STAGE, K>(), x, count, epi, s);
   } else {
     return launch_f64_persistent(f64_split_kernel<NMAX, BLOCK, TILE, MakeEpi, TWO>, grid_cap, BLOCK, TILE, 0, x,
                                  count, epi, s);
   }
 }
 
-template <int NMAX, typename MakeEpi, bool TWO = false, int STAGE = 0>
+template <int NMAX, typename MakeEpi, bool TWO = false, int STAGE = 0, int K = 2>
 int launch_f64_epi(const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s) {
   if (count <= kF64SmallCount)
-    return launch_f64_shape<NMAX, kF64SmallBlock, kF64SmallTile, MakeEpi, TWO, STAGE>(x, count, epi, s);
-  return launch_f64_shape<NMAX, kF64Block, kF64Tile, MakeEpi, TWO, STAGE>(x, count, epi, s);
+    return launch_f64_shape<NMAX, kF64SmallBlock, kF64SmallTile, MakeEpi, TWO, STAGE, K>(x, count, epi, s);
+  return launch_f64_shape<NMAX, kF64Block, kF64Tile, MakeEpi, TWO, STAGE, K>(x, count, epi, s);
 }
 
 // Orders staged per flush of the row-staging buffer (rows of n_max >= 12,
@@ -625,7 +604,8 @@ int launch_f64_grad_recompute(const double *x, int64_t count, const double *g, i
 // Two-point evaluation (Trick B): rows as launch_f64.
 template <int NMAX>
 int launch_f64_two_point(const double *x, int64_t count, double *out, cudaStream_t s) {
-  return launch_f64_epi<NMAX, MakeStore<NMAX + 1>, true>(x, count, MakeStore<NMAX + 1>{out}, s);
+  return launch_f64_epi<NMAX, MakeStore<NMAX + 1>, true, (NMAX >= 12 ? kF64StageOrders : 0)>(
+      x, count, MakeStore<NMAX + 1>{out}, s);
 }
 
 template <int NMAX>
