@@ -11,6 +11,8 @@
 int boys_f64_dispatch_p0(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
 int boys_f64_dispatch_p1(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
 int boys_f64_dispatch_p2(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
+int boys_f64_dispatch_p3(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
+int boys_f64_dispatch_p4(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
 int boys_f32_dispatch_p0(int n_max, const float *x, int64_t count, float *out, cudaStream_t s);
 int boys_grad_dispatch_p0(int n_max, const double *x, int64_t count, const double *g, int64_t g_row, int64_t g_col,
                           double *grad, cudaStream_t s);
@@ -24,6 +26,9 @@ int boys_contract_f32_dispatch(int n_max, const float *x, int64_t count, const f
                                float *out, cudaStream_t s);
 int boys_two_point_dispatch_p0(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
 int boys_two_point_dispatch_p1(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
+int boys_two_point_dispatch_p2(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
+int boys_two_point_dispatch_p3(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
+int boys_two_point_dispatch_p4(int n_max, const double *x, int64_t count, double *out, cudaStream_t s);
 int boys_grad_saved_launch(const double *F, int64_t ld_F, const double *g, int64_t g_row, int64_t g_col,
                            int64_t count, int n_max, double *grad, cudaStream_t s);
 int boys_f32_dispatch_p1(int n_max, const float *x, int64_t count, float *out, cudaStream_t s);
@@ -104,9 +109,12 @@ int helper_for_current_device(HelperStream **out) {
 
 int dispatch_f64(int n_max, const double *x, int64_t count, double *out, cudaStream_t s) {
   int rc;
+  // the order ranges of boys_f64_p0.cu .. boys_f64_p4.cu
   if (n_max <= 12) rc = boys_f64_dispatch_p0(n_max, x, count, out, s);
-  else if (n_max <= 24) rc = boys_f64_dispatch_p1(n_max, x, count, out, s);
-  else rc = boys_f64_dispatch_p2(n_max, x, count, out, s);
+  else if (n_max <= 20) rc = boys_f64_dispatch_p1(n_max, x, count, out, s);
+  else if (n_max <= 26) rc = boys_f64_dispatch_p2(n_max, x, count, out, s);
+  else if (n_max <= 31) rc = boys_f64_dispatch_p3(n_max, x, count, out, s);
+  else rc = boys_f64_dispatch_p4(n_max, x, count, out, s);
   return rc < 0 ? BOYS_ERR_NMAX : rc;
 }
 
@@ -261,8 +269,12 @@ boys_status boys_eval_f64_two_point(const double *x, int64_t count, int n_max, d
   int rc = check_rows(x, count, n_max, kMaxNF64, out, sizeof(double));
   if (rc || count == 0) return (boys_status)rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  rc = n_max <= 20 ? boys_two_point_dispatch_p0(n_max, x, count, out, s)
-                   : boys_two_point_dispatch_p1(n_max, x, count, out, s);
+  // the order ranges of boys_two_point_p0.cu .. boys_two_point_p4.cu
+  if (n_max <= 14) rc = boys_two_point_dispatch_p0(n_max, x, count, out, s);
+  else if (n_max <= 21) rc = boys_two_point_dispatch_p1(n_max, x, count, out, s);
+  else if (n_max <= 27) rc = boys_two_point_dispatch_p2(n_max, x, count, out, s);
+  else if (n_max <= 32) rc = boys_two_point_dispatch_p3(n_max, x, count, out, s);
+  else rc = boys_two_point_dispatch_p4(n_max, x, count, out, s);
   return (boys_status)(rc < 0 ? BOYS_ERR_NMAX : rc);
 }
 

@@ -388,7 +388,16 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
     const int q = c + lane;
     if constexpr (STAGED) {
       // the whole warp takes part; lanes past the end of the list compute a
-      // dummy argument and store nothing
+      // dummy argument and store nothing (with 32 entries or fewer left, one
+      // entry per lane)
+      if constexpr (ILP == 2) {
+        if (nlo - c <= 32) {
+          const int j1[1] = {q < nlo ? (int)sm.lst[q] : -1};
+          const double x1[1] = {j1[0] >= 0 ? sm.xs[j1[0]] : 1.0};
+          f64_formula_staged<NTOP, NMAX, STAGE, 1, TWO>(x1, j1, epi.out, stg, sm.tab64, lane);
+          continue;
+        }
+      }
       int j[ILP];
       double xv[ILP];
 #pragma unroll
@@ -431,6 +440,14 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
     if (c >= nhi) break;
     const int q = c + lane;
     if constexpr (STAGED) {
+      if constexpr (ILP == 2) {
+        if (nhi - c <= 32) {
+          const int j1[1] = {q < nhi ? (int)sm.lst[TILE - 1 - q] : -1};
+          const double x1[1] = {j1[0] >= 0 ? sm.xs[j1[0]] : 1.0};
+          f64_asymptote_staged<NMAX, STAGE, 1>(x1, j1, epi.out, stg, lane);
+          continue;
+        }
+      }
       int j[ILP];
       double xv[ILP];
 #pragma unroll

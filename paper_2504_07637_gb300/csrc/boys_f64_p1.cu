@@ -1,4 +1,4 @@
-// FP64 forward instantiations for n_max = 13..24 (split across translation units to build in parallel).
+// FP64 forward instantiations for n_max = 13..20 (split across translation units to build in parallel).
 #include "boys_f64.cuh"
 
 int boys_f64_dispatch_p1(int n_max, const double *x, int64_t count, double *out, cudaStream_t s) {
@@ -11,10 +11,6 @@ int boys_f64_dispatch_p1(int n_max, const double *x, int64_t count, double *out,
     BOYS_F64_CASE(18)
     BOYS_F64_CASE(19)
     BOYS_F64_CASE(20)
-    BOYS_F64_CASE(21)
-    BOYS_F64_CASE(22)
-    BOYS_F64_CASE(23)
-    BOYS_F64_CASE(24)
     default:
       return -1;
   }

@@ -1,20 +1,14 @@
-// FP64 forward instantiations for n_max = 25..36 (split across translation units to build in parallel).
+// FP64 forward instantiations for n_max = 21..26 (split across translation units to build in parallel).
 #include "boys_f64.cuh"
 
 int boys_f64_dispatch_p2(int n_max, const double *x, int64_t count, double *out, cudaStream_t s) {
   switch (n_max) {
+    BOYS_F64_CASE(21)
+    BOYS_F64_CASE(22)
+    BOYS_F64_CASE(23)
+    BOYS_F64_CASE(24)
     BOYS_F64_CASE(25)
     BOYS_F64_CASE(26)
-    BOYS_F64_CASE(27)
-    BOYS_F64_CASE(28)
-    BOYS_F64_CASE(29)
-    BOYS_F64_CASE(30)
-    BOYS_F64_CASE(31)
-    BOYS_F64_CASE(32)
-    BOYS_F64_CASE(33)
-    BOYS_F64_CASE(34)
-    BOYS_F64_CASE(35)
-    BOYS_F64_CASE(36)
     default:
       return -1;
   }

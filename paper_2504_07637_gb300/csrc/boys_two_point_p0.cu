@@ -1,4 +1,5 @@
-// Two-point (Trick B) instantiations for n_max = 2..20: closed forms at n_top and at n_top(n_max/2).
+// Two-point (Trick B) instantiations for n_max = 2..14 (closed forms at n_top and at n_top(n_max/2);
+// split across translation units to build in parallel).
 #include "boys_f64.cuh"
 
 int boys_two_point_dispatch_p0(int n_max, const double *x, int64_t count, double *out, cudaStream_t s) {
@@ -16,12 +17,6 @@ int boys_two_point_dispatch_p0(int n_max, const double *x, int64_t count, double
     BOYS_F64_TWO_CASE(12)
     BOYS_F64_TWO_CASE(13)
     BOYS_F64_TWO_CASE(14)
-    BOYS_F64_TWO_CASE(15)
-    BOYS_F64_TWO_CASE(16)
-    BOYS_F64_TWO_CASE(17)
-    BOYS_F64_TWO_CASE(18)
-    BOYS_F64_TWO_CASE(19)
-    BOYS_F64_TWO_CASE(20)
     default:
       return -1;
   }
