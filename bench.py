@@ -562,11 +562,16 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
     res = {"ms": ms, "values": count * (n_max + 1), "clocks": clk, "x_host": x_host}
     hbm_peak, hbm_src = measured_peaks()
     hbm_gbs = roofline.bytes_per_arg(n_max, esz) * count / (ms / 1e3) / 1e9
-    if not f32 and rates is not None and not wl.get("two_point"):
-        n_top = _capi.load().boys_top_order_f64(n_max)
-        z = _capi.load().boys_cutoff(n_top, 53)
+    if not f32 and rates is not None:
+        lib = _capi.load()
+        n_top = lib.boys_top_order_f64(n_max)
+        z = lib.boys_cutoff(n_top, 53)
         fb = float(np.mean(x_host <= z))
-        below, above = roofline.f64_counts(n_max, n_top)
+        if wl.get("two_point"):  # Trick B: n_bar = n_max / 2, closed forms at n_top and n_top(n_bar)
+            n_bar = n_max // 2
+            below, above = roofline.f64_counts_two_point(n_max, n_top, n_bar, lib.boys_top_order_f64(n_bar))
+        else:
+            below, above = roofline.f64_counts(n_max, n_top)
         t_arg = sum((fb * below[k] + (1 - fb) * above[k]) / rates[k] for k in ("fma", "div", "sqrt", "exp", "rsqrt"))
         achieved = t_arg * rates["fma"] * count / (ms / 1e3) / 1e12
         peak = rates["fma"] / 1e12
@@ -576,7 +581,7 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
             "peak": round(peak, 5),
             "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4),
-            "traffic": traffic_record(f"f64_split_kernel<{n_max}>/scale_2^26"),
+            "traffic": None if wl.get("two_point") else traffic_record(f"f64_split_kernel<{n_max}>/scale_2^26"),
             "note": "FP64-pipe instruction equivalents per second (1 per add/mul/fma; exp, sqrt, rsqrt and div "
             "weighted by their measured cost) vs the DFMA rate measured in this run; "
             f"{fb:.3f} of arguments below z_{{{n_top},53}}",

@@ -39,11 +39,10 @@ def square_multiply_ops(k: int) -> int:
     return (k.bit_length() - 1) + (bin(k).count("1") - 1)
 
 
-def f64_counts(n_max: int, n_top: int) -> tuple[dict, dict]:
-    """(below-cut-off, above-cut-off) operation counts per argument, in the
-    form the double kernels evaluate them: sqrt(Q) as Q rsqrt(Q); D^{-s} as
-    rsqrt(D)^{2n+1} for n_top <= 13, else (1/D)^n (1/D) rsqrt(1/D); the
-    asymptote's 1/x as rsqrt(x)^2 for n_max <= 12."""
+def _closed_form_counts(n_top: int) -> dict:
+    """Operations of F_{n_top} by the closed form (Eq. "fq") given e^{-x}:
+    Q~ in root-product form and one division u/v, Q^n and Q rsqrt(Q), D, and
+    D^{-s} as rsqrt(D)^{2n+1} for n_top <= 13, else (1/D)^n (1/D) rsqrt(1/D)."""
     rec = _fits(53)[n_top]
     pw = square_multiply_ops(n_top)
     fma = root_product_ops(rec["u"]) + root_product_ops(rec["v"]) + 4  # Q~
@@ -54,16 +53,44 @@ def f64_counts(n_max: int, n_top: int) -> tuple[dict, dict]:
     else:
         fma += pw + 1 + 2  # w^n, w rsqrt(w), c w^n and the product
         rsq, div = 2, 2
-    fma += 2 * n_top  # recursion
-    below = {"fma": fma, "div": div, "sqrt": 0, "exp": 1, "rsqrt": rsq}
-    above = {
+    return {"fma": fma, "div": div, "sqrt": 0, "exp": 0, "rsqrt": rsq}
+
+
+def _asymptote_counts(n_max: int) -> dict:
+    """Operations of the asymptote row (Eq. "limf1"): one reciprocal square
+    root, 1/x as rsqrt(x)^2 for n_max <= 12 (else a division), and two
+    operations per order."""
+    return {
         "fma": 1 + (1 if n_max <= 12 else 0) + 2 * n_max,
         "div": 0 if n_max <= 12 else 1,
         "sqrt": 0,
         "exp": 0,
         "rsqrt": 1,
     }
-    return below, above
+
+
+def f64_counts(n_max: int, n_top: int) -> tuple[dict, dict]:
+    """(below-cut-off, above-cut-off) operation counts per argument, in the
+    form the double kernels evaluate them: the closed form at n_top, one
+    exponential and two operations per step of the downward recursion (Eq.
+    "r") below the cut-off; the asymptote above it."""
+    below = _closed_form_counts(n_top)
+    below["exp"] = 1
+    below["fma"] += 2 * n_top  # recursion
+    return below, _asymptote_counts(n_max)
+
+
+def f64_counts_two_point(n_max: int, n_top: int, n_bar: int, n_top_lo: int) -> tuple[dict, dict]:
+    """As f64_counts for the two-point evaluation (Trick B of Sec. 3): closed
+    forms at n_top and at n_top_lo sharing one exponential, the recursion
+    from n_top down to n_bar + 1 and the one from n_top_lo down to 0."""
+    below = _closed_form_counts(n_top)
+    lo = _closed_form_counts(n_top_lo)
+    for k in below:
+        below[k] += lo[k]
+    below["exp"] = 1
+    below["fma"] += 2 * (n_top - (n_bar + 1)) + 2 * n_top_lo
+    return below, _asymptote_counts(n_max)
 
 
 def bytes_per_arg(n_max: int, elem: int = 8) -> int:
