@@ -755,6 +755,8 @@ def main():
             if "roofline" in r:
                 suite[name]["roofline_bound"] = r["roofline"]["bound"]
                 suite[name]["roofline_frac"] = r["roofline"]["frac"]
+        # the float path against the double one on the same arguments and order (n_max = 8)
+        suite["scale_f32_n8"]["speedup_vs_f64_n8"] = round(suite["scale_f32_n8"]["value"] / value, 2)
         for name in ("contract_f64_n8", "contract_f32_n8"):
             suite[name] = measure_contract(WORKLOADS[name], 10, 3, device, seed, rates=rates)
         sub = argparse.Namespace(steps=10, warmup=3, gpus=1)
