@@ -69,7 +69,7 @@ def test_plain_workload_n8(lib, oracle_mod, record_property):
 
 
 @pytest.mark.parametrize("n_max", list(range(0, 17)))
-def test_every_order(lib, oracle_mod, n_max):
+def test_every_order(lib, oracle_mod, n_max, record_property):
     rng = np.random.default_rng(300 + n_max)
     z = lib.cutoff(lib.top_order_f32(n_max), 24)
     x = np.concatenate(
@@ -80,7 +80,9 @@ def test_every_order(lib, oracle_mod, n_max):
         ]
     )
     got, xf = _gpu(lib, x, n_max)
-    assert _check(got, oracle_mod.boys(xf.astype(np.float64), n_max)).max() <= TOL
+    rel = _check(got, oracle_mod.boys(xf.astype(np.float64), n_max))
+    record_property("max_rel_err_per_m", _per_m(rel))
+    assert rel.max() <= TOL
 
 
 def test_special_arguments(lib, oracle_mod):

@@ -65,7 +65,7 @@ def test_plain_workload_n8(lib, oracle_mod, record_property):
 
 
 @pytest.mark.parametrize("n_max", list(range(0, 37)))
-def test_every_order(lib, oracle_mod, n_max):
+def test_every_order(lib, oracle_mod, n_max, record_property):
     # several tiles plus a ragged tail; arguments across [0, 2 z] and beyond
     rng = np.random.default_rng(100 + n_max)
     z = lib.cutoff(lib.top_order_f64(n_max), 53)
@@ -78,7 +78,9 @@ def test_every_order(lib, oracle_mod, n_max):
     )
     got = _gpu(lib, x, n_max)
     ref = oracle_mod.boys(x, n_max)
-    assert _relerr(got, ref).max() <= TOL
+    rel = _relerr(got, ref)
+    record_property("max_rel_err_per_m", _per_m(rel))
+    assert rel.max() <= TOL
 
 
 def test_special_arguments(lib, oracle_mod):
@@ -220,14 +222,16 @@ def test_host_pipeline_matches_device_path(lib, pinned):
 
 
 @pytest.mark.parametrize("n_max", [2, 9, 16, 24, 36])
-def test_two_point_within_bound(lib, oracle_mod, n_max):
+def test_two_point_within_bound(lib, oracle_mod, n_max, record_property):
     import torch
 
     rng = np.random.default_rng(700 + n_max)
     z = lib.cutoff(lib.top_order_f64(n_max), 53)
     x = np.concatenate([np.exp(rng.uniform(math.log(1e-8), math.log(2 * z), 4000)), [0.0, 1e6, np.inf]])
     got = lib.boys(torch.from_numpy(x).cuda(), n_max, two_point=True).cpu().numpy()
-    assert _relerr(got, oracle_mod.boys(x, n_max)).max() <= TOL
+    rel = _relerr(got, oracle_mod.boys(x, n_max))
+    record_property("max_rel_err_per_m", _per_m(rel))
+    assert rel.max() <= TOL
 
 
 def test_two_point_improves_low_orders(lib, oracle_mod):
