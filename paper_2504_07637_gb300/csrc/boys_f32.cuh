@@ -30,15 +30,16 @@ __device__ __forceinline__ bool below_cutoff_f32(float v, unsigned zbits) {
 
 // MODE 0 writes rows F_0..F_NMAX; MODE 1 is the fused contraction
 // out[i] = sum_m c[i, m] F_m(x_i) (one float per argument).
-template <int NMAX, int MODE = 0>
+// BLOCK_ / TILE_ = 0: the default shape below.
+template <int NMAX, int MODE = 0, int BLOCK_ = 0, int TILE_ = 0>
 struct F32Tile {
   static constexpr int W = NMAX + 1;
   static constexpr int WO = MODE == 0 ? W : 1;  // floats written per argument
   // 8 arguments per thread; small blocks keep the closed-form list's last
   // round of a tile well filled (about 30% of a tile is listed, and a block
   // waits for its slowest warp), measured best on GB300 for each band
-  static constexpr int TILE = W <= 9 || MODE == 1 ? 1024 : 512;
-  static constexpr int BLOCK = W <= 9 || MODE == 1 ? 128 : 64;
+  static constexpr int TILE = TILE_ ? TILE_ : (W <= 9 || MODE == 1 ? 1024 : 512);
+  static constexpr int BLOCK = BLOCK_ ? BLOCK_ : (W <= 9 || MODE == 1 ? 128 : 64);
   // rows[TILE*WO] floats, xs[TILE] floats, tab[64] floats, lst[TILE] u16
   static constexpr size_t kSmem = sizeof(float) * (TILE + TILE * WO + 64) + sizeof(unsigned short) * TILE;
 };
@@ -70,10 +71,11 @@ __device__ __forceinline__ void f32_emit(float *__restrict__ rows, int j, int64_
   }
 }
 
-template <int NMAX, int MODE>
-__global__ void __launch_bounds__(F32Tile<NMAX, MODE>::BLOCK) f32_split_kernel(const float *__restrict__ x, int64_t count,
-                                                        float *__restrict__ out, const F32Coef cf) {
-  using P = F32Tile<NMAX, MODE>;
+template <int NMAX, int MODE, int BLOCK_ = 0, int TILE_ = 0>
+__global__ void __launch_bounds__(F32Tile<NMAX, MODE, BLOCK_, TILE_>::BLOCK)
+    f32_split_kernel(const float *__restrict__ x, int64_t count, float *__restrict__ out, const F32Coef cf) {
+  using P = F32Tile<NMAX, MODE, BLOCK_, TILE_>;
+  static_assert(P::BLOCK >= 64 && P::TILE % P::BLOCK == 0 && P::TILE <= 65536, "shape");  // 64: the table load
   constexpr int NTOP = f32_top_order(NMAX);
   constexpr int W = P::W, WO = P::WO, TILE = P::TILE, BLOCK = P::BLOCK;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -154,10 +156,10 @@ __global__ void __launch_bounds__(F32Tile<NMAX, MODE>::BLOCK) f32_split_kernel(c
   if (threadIdx.x == 0) bulk_wait_all();
 }
 
-template <int NMAX, int MODE = 0>
+template <int NMAX, int MODE = 0, int BLOCK_ = 0, int TILE_ = 0>
 int launch_f32(const float *x, int64_t count, float *out, cudaStream_t s, F32Coef cf = F32Coef{nullptr, 0, 0}) {
-  using P = F32Tile<NMAX, MODE>;
-  auto k = f32_split_kernel<NMAX, MODE>;
+  using P = F32Tile<NMAX, MODE, BLOCK_, TILE_>;
+  auto k = f32_split_kernel<NMAX, MODE, BLOCK_, TILE_>;
   static int grid_cap = 0;
   if (grid_cap == 0) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::kSmem) != cudaSuccess)
