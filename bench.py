@@ -265,6 +265,10 @@ def microbench(capi, device):
     return rates
 
 
+# FP64 nominal rate of GB300: 1.25 TFLOP/s, i.e. 0.625 T fused multiply-adds per second
+F64_NOMINAL_TFMA = 0.625
+
+
 def traffic_record(kernel_key: str):
     """DRAM bytes per launch from the committed ncu summary, if it still matches the sources."""
     import hashlib
@@ -587,6 +591,9 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
             f"{fb:.3f} of arguments below z_{{{n_top},53}}",
             "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 4),
                     "peak_source": hbm_src},
+            "nominal": {"peak": F64_NOMINAL_TFMA, "frac": round(achieved / F64_NOMINAL_TFMA, 4),
+                        "source": "GB300 FP64 1.25 TFLOP/s nominal = 0.625 T FMA/s (2 DFMA per clock per SM at "
+                        "152 SMs x 2.07 GHz)"},
             "measured_rates_gops": {k: round(v / 1e9, 2) for k, v in rates.items()},
         }
     elif f32:
