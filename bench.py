@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--workload", default="scale_f64_n8", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip microbenchmarks and e2e (for profiling)")
+    ap.add_argument("--peak-sweep", action="store_true",
+                    help="print the DFMA rate over chains per thread x blocks per SM, then the library's "
+                    "microbenchmark once, and exit")
     return ap.parse_args()
 
 
@@ -711,8 +714,43 @@ def measure_plain(device, rates):
             "queued: 200 calls back to back"}
 
 
+def peak_sweep():
+    """DFMA rate (G/s) over chains per thread x blocks of 256 threads per SM:
+    whether the roofline's measured peak is the GPU's ceiling."""
+    import torch
+
+    from paper_2504_07637_gb300 import _capi
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    stream = torch.cuda.current_stream(dev)
+    iters, table = 2048, {}
+    for chains in (1, 2, 4, 8, 16):
+        for per_sm in (1, 2, 4, 8):
+            blocks = sms * per_sm
+            _capi.call("boys_microbench_dfma", chains, 64, sink.data_ptr(), blocks, stream.cuda_stream)
+            best = None
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _capi.call("boys_microbench_dfma", chains, iters, sink.data_ptr(), blocks, stream.cuda_stream)
+                e1.record(stream)
+                e1.synchronize()
+                dt = e0.elapsed_time(e1) / 1e3
+                best = dt if best is None else min(best, dt)
+            table[f"{chains}x{per_sm}"] = round(blocks * 256 * iters * chains / best / 1e9, 1)
+    rates = microbench(_capi, dev)
+    print(json.dumps({"dfma_gops_chains_x_blocks_per_sm": table, "microbench_fma_gops": round(rates["fma"] / 1e9, 1)}),
+          flush=True)
+
+
 def main():
     args = parse()
+    if args.peak_sweep:
+        peak_sweep()
+        return
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)

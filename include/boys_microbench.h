@@ -37,6 +37,13 @@ int boys_microbench_launch(int op, int64_t iters, double *sink, int blocks, void
 /* Independent operations per thread and iteration (the chain count). */
 int boys_microbench_ops_per_thread_iter(void);
 
+/* Double fused multiply-adds only, with `chains` independent chains per
+ * thread (1, 2, 4, 8 or 16; anything else returns BOYS_ERR_ARG): `blocks` x
+ * 256 threads, each running `iters` x `chains` fma on `stream`.  Sweeping
+ * chains and blocks shows whether the DFMA rate of boys_microbench_launch is
+ * the GPU's ceiling rather than a latency limit.  Returns a boys_status. */
+int boys_microbench_dfma(int chains, int64_t iters, double *sink, int blocks, void *stream);
+
 /* out[i] = e^{-x[i]} by the library's own exponential (Tang's table-driven
  * method), for testing it against a reference; valid for 0 <= x <= 700.
  * x, out: device arrays of n doubles.  Returns a boys_status. */

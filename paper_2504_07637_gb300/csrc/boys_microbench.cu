@@ -49,6 +49,29 @@ __global__ void __launch_bounds__(256) micro_kernel(int64_t iters, double *sink)
   if (acc == 123.456) sink[0] = acc;  // never true; keeps the chains live
 }
 
+// FMA-only kernel with C independent chains per thread
+template <int C>
+__global__ void __launch_bounds__(256) dfma_chains_kernel(int64_t iters, double *sink) {
+  double a[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) a[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+  const double ka = 0.9999999, kb = 1e-7;
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) a[c] = fma(a[c], ka, kb);
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < C; ++c) acc += a[c];
+  if (acc == 123.456) sink[0] = acc;  // never true; keeps the chains live
+}
+
+template <int C>
+int launch_chains(int64_t iters, double *sink, int blocks, cudaStream_t s) {
+  dfma_chains_kernel<C><<<blocks, 256, 0, s>>>(iters, sink);
+  return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
+}
+
 template <int OP>
 int launch(int64_t iters, double *sink, int blocks, cudaStream_t s) {
   micro_kernel<OP><<<blocks, 256, 0, s>>>(iters, sink);
@@ -77,6 +100,19 @@ extern "C" int boys_microbench_launch(int op, int64_t iters, double *sink, int b
 }
 
 extern "C" int boys_microbench_ops_per_thread_iter(void) { return kChains; }
+
+extern "C" int boys_microbench_dfma(int chains, int64_t iters, double *sink, int blocks, void *stream) {
+  if (iters < 0 || blocks < 1 || !sink) return BOYS_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (chains) {
+    case 1: return launch_chains<1>(iters, sink, blocks, s);
+    case 2: return launch_chains<2>(iters, sink, blocks, s);
+    case 4: return launch_chains<4>(iters, sink, blocks, s);
+    case 8: return launch_chains<8>(iters, sink, blocks, s);
+    case 16: return launch_chains<16>(iters, sink, blocks, s);
+    default: return BOYS_ERR_ARG;
+  }
+}
 
 namespace {
 __global__ void exp_neg_kernel(const double *__restrict__ x, int64_t n, double *__restrict__ out) {
