@@ -58,6 +58,19 @@ def _per_m(rel):
     return [float(f"{v:.3g}") for v in rel.max(axis=0)]
 
 
+def _table1_eps_bar_n(n):
+    """Table I's finite-precision accuracy of F_n (single column eps_n_bar, in
+    bits): the paper's own rounding level after its recursion."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1_accuracy_bits.txt")
+    for line in open(path):
+        f = line.split()
+        if f and not line.startswith("#") and int(f[0]) == n:
+            return float(f[9])
+    raise KeyError(n)
+
+
 def test_plain_workload_n8(lib, oracle_mod, record_property):
     from paper_2504_07637_gb300 import workloads
 
@@ -83,6 +96,9 @@ def test_every_order(lib, oracle_mod, n_max, record_property):
     rel = _check(got, oracle_mod.boys(xf.astype(np.float64), n_max))
     record_property("max_rel_err_per_m", _per_m(rel))
     assert rel.max() <= TOL
+    # at least as accurate as the paper's own evaluation (Table I, eps_n_bar),
+    # within 1 bit for the different sample points and rounding
+    assert -math.log2(max(rel.max(), 2.0**-60)) >= _table1_eps_bar_n(n_max) - 1.0
 
 
 def test_special_arguments(lib, oracle_mod):
