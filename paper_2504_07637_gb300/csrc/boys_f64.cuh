@@ -15,6 +15,11 @@
 //    |r| <= ln2/128, about 10 FP64 operations.
 //  * Half-integer powers use the reciprocal square root where the rounding
 //    budget allows it.
+//  * From n_max = 12 on, a lane takes two list entries (two independent
+//    recursion chains), and the rows of a store leave through a per-warp
+//    shared-memory staging buffer in row order.  Rows stored straight from
+//    registers touch 32 sectors per warp instruction, and those stores back
+//    up into the FP64 instruction stream.
 #pragma once
 
 #include "boys_coeffs_f64.inc"
@@ -143,7 +148,7 @@ __device__ __forceinline__ void f64_asymptote(const double x, double (&F)[NMAX +
   }
 }
 
-// Compile-time loop: f(std::integral_constant<int, I>) for I = BEGIN, BEGIN + STEP, ... up to END (excluded).
+// Compile-time loop: f(std::integral_constant<int, i>) for i = I, I + STEP, ... while i has not reached END.
 template <int I, int END, int STEP, typename Fn>
 __device__ __forceinline__ void static_for(Fn &&f) {
   if constexpr ((STEP > 0 && I < END) || (STEP < 0 && I > END)) {
@@ -329,9 +334,10 @@ struct F64TileSmem {
 };
 
 // One tile of nel <= TILE arguments xt[0..nel): classify, build the two lists,
-// evaluate each list 32 entries per warp request and hand rows to epi.
-// All threads of the block call it; it begins and ends with a barrier.
-
+// evaluate each list in warp requests (32 entries, 64 with two per lane) and
+// hand the rows to epi (STAGE > 0: stage and store them; stage = the block's
+// staging buffer).  All threads of the block call it; it begins and ends with
+// a barrier.
 // ALLOW_ILP = false keeps one list entry per lane at every order (a kernel
 // that switches between orders keeps the register count of the smallest).
 template <int NMAX, int BLOCK, int TILE, typename Epi, bool TWO = false, bool ALLOW_ILP = true, int STAGE = 0,
