@@ -25,8 +25,9 @@ __global__ void __launch_bounds__(256) grad_saved_kernel(const double *__restric
 
 int boys_grad_saved_launch(const double *F, int64_t ld_F, const double *g, int64_t g_row, int64_t g_col,
                            int64_t count, int n_max, double *grad, cudaStream_t s) {
-  static int grid_cap = 0;
-  if (grid_cap == 0) grid_cap = boys::persistent_grid(grad_saved_kernel, 256, 0, INT64_MAX);
+  static std::atomic<int> cache[boys::kMaxCachedDevices];
+  const int grid_cap = boys::device_setup(grad_saved_kernel, 256, 0, 0, true, cache);
+  if (grid_cap == 0) return BOYS_ERR_CUDA;
   const int64_t blocks = (count + 255) / 256;
   const int grid = (int)(blocks < grid_cap ? blocks : grid_cap);
   grad_saved_kernel<<<grid, 256, 0, s>>>(F, ld_F, g, g_row, g_col, count, n_max + 1, grad);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/boys.h"
 
 namespace boys {
@@ -46,6 +48,34 @@ __host__ __device__ constexpr int f32_top_order(int n_max) { return n_max <= 8 ?
 constexpr int kMaxNF32 = 16;
 
 // Persistent-grid size for a kernel: resident blocks per SM times SM count.
+template <typename Kernel>
+inline int persistent_grid(Kernel k, int block, size_t smem, int64_t tiles);
+
+// Per-device launch setup of one kernel, done on its first launch on each
+// device (a kernel's attributes belong to the device's context, so one
+// process driving several GPUs needs them per device): the opt-in to
+// dyn_attr bytes of dynamic shared memory (0: none needed) and, when
+// want_grid, the persistent grid for dyn_smem bytes.  cache holds one slot
+// per device (0 = not set up).  Returns the grid (1 when !want_grid), or 0
+// on a CUDA error.
+constexpr int kMaxCachedDevices = 64;
+template <typename Kernel>
+inline int device_setup(Kernel k, int block, size_t dyn_smem, size_t dyn_attr, bool want_grid,
+                        std::atomic<int> (&cache)[kMaxCachedDevices]) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const bool cached = dev >= 0 && dev < kMaxCachedDevices;
+  if (cached) {
+    const int g = cache[dev].load(std::memory_order_acquire);
+    if (g) return g;
+  }
+  if (dyn_attr > 0 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_attr) != cudaSuccess)
+    return 0;
+  const int g = want_grid ? persistent_grid(k, block, dyn_smem, INT64_MAX) : 1;
+  if (cached) cache[dev].store(g, std::memory_order_release);
+  return g;
+}
+
 template <typename Kernel>
 inline int persistent_grid(Kernel k, int block, size_t smem, int64_t tiles) {
   int dev = 0, sms = 0, per_sm = 0;

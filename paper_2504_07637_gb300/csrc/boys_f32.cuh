@@ -160,12 +160,9 @@ template <int NMAX, int MODE = 0, int BLOCK_ = 0, int TILE_ = 0>
 int launch_f32(const float *x, int64_t count, float *out, cudaStream_t s, F32Coef cf = F32Coef{nullptr, 0, 0}) {
   using P = F32Tile<NMAX, MODE, BLOCK_, TILE_>;
   auto k = f32_split_kernel<NMAX, MODE, BLOCK_, TILE_>;
-  static int grid_cap = 0;
-  if (grid_cap == 0) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::kSmem) != cudaSuccess)
-      return BOYS_ERR_CUDA;
-    grid_cap = persistent_grid(k, P::BLOCK, P::kSmem, INT64_MAX);
-  }
+  static std::atomic<int> cache[kMaxCachedDevices];
+  const int grid_cap = device_setup(k, P::BLOCK, P::kSmem, P::kSmem, true, cache);
+  if (grid_cap == 0) return BOYS_ERR_CUDA;
   const int64_t tiles = (count + P::TILE - 1) / P::TILE;
   const int grid = (int)(tiles < grid_cap ? tiles : grid_cap);
   k<<<grid, P::BLOCK, P::kSmem, s>>>(x, count, out, cf);

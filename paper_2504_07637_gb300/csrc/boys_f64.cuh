@@ -572,16 +572,12 @@ constexpr int kF64Block = 256, kF64Tile = 2048;
 constexpr int64_t kF64SmallCount = 1 << 20;
 constexpr int kF64SmallBlock = 128, kF64SmallTile = 256;
 
-// Launch kernel k on a persistent grid (grid_cap: its resident blocks, found
-// on the first call).
+// Launch kernel k on a persistent grid (set up per device through cache).
 template <typename Kernel, typename MakeEpi>
-int launch_f64_persistent(Kernel k, int &grid_cap, int block, int tile, size_t dyn, const double *x, int64_t count,
-                          const MakeEpi &epi, cudaStream_t s) {
-  if (grid_cap == 0) {
-    if (dyn > 0 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
-      return BOYS_ERR_CUDA;
-    grid_cap = persistent_grid(k, block, dyn, INT64_MAX);
-  }
+int launch_f64_persistent(Kernel k, std::atomic<int> (&cache)[kMaxCachedDevices], int block, int tile, size_t dyn,
+                          const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s) {
+  const int grid_cap = device_setup(k, block, dyn, dyn, true, cache);
+  if (grid_cap == 0) return BOYS_ERR_CUDA;
   const int64_t tiles = (count + tile - 1) / tile;
   const int grid = (int)(tiles < grid_cap ? tiles : grid_cap);
   k<<<grid, block, dyn, s>>>(x, count, epi);
@@ -590,12 +586,12 @@ int launch_f64_persistent(Kernel k, int &grid_cap, int block, int tile, size_t d
 
 template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO, int STAGE = 0, int K = 2>
 int launch_f64_shape(const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s) {
-  static int grid_cap = 0;
+  static std::atomic<int> cache[kMaxCachedDevices];
   if constexpr (STAGE > 0) {
-    return launch_f64_persistent(f64_staged_kernel<NMAX, BLOCK, TILE, MakeEpi, TWO, STAGE, K>, grid_cap, BLOCK, TILE,
+    return launch_f64_persistent(f64_staged_kernel<NMAX, BLOCK, TILE, MakeEpi, TWO, STAGE, K>, cache, BLOCK, TILE,
                                  f64_stage_bytes<BLOCK, STAGE, K>(), x, count, epi, s);
   } else {
-    return launch_f64_persistent(f64_split_kernel<NMAX, BLOCK, TILE, MakeEpi, TWO>, grid_cap, BLOCK, TILE, 0, x,
+    return launch_f64_persistent(f64_split_kernel<NMAX, BLOCK, TILE, MakeEpi, TWO>, cache, BLOCK, TILE, 0, x,
                                  count, epi, s);
   }
 }

@@ -179,13 +179,9 @@ int launch_ragged(const RaggedArgs &a, cudaStream_t s) {
   if (cudaPeekAtLastError() != cudaSuccess) return BOYS_ERR_CUDA;
   const size_t dyn = a.num_requests < kSmemPrefixMax ? sizeof(int64_t) * (size_t)(a.num_requests + 1) : 0;
   auto k = ragged_eval_kernel<BLOCK, TILE>;
-  static int configured = 0;
-  if (!configured) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(int64_t) * kSmemPrefixMax)) != cudaSuccess)
-      return BOYS_ERR_CUDA;
-    configured = 1;
-  }
+  // the shared-memory opt-in once per device; the grid depends on this call's prefix size
+  static std::atomic<int> configured[boys::kMaxCachedDevices];
+  if (boys::device_setup(k, BLOCK, 0, sizeof(int64_t) * kSmemPrefixMax, false, configured) == 0) return BOYS_ERR_CUDA;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
