@@ -118,6 +118,27 @@ def test_special_arguments(lib, oracle_mod):
     assert np.max(np.abs(zero * (2 * np.arange(37) + 1) - 1)) <= TOL
 
 
+@pytest.mark.parametrize("two_point", [False, True])
+@pytest.mark.parametrize("n_max", [8, 16, 36])
+def test_domain_convention_every_layout(lib, n_max, two_point):
+    # negative, NaN and infinite arguments mixed with ordinary ones, enough of
+    # them to fill whole staged requests of the asymptote list at high orders
+    import torch
+
+    rng = np.random.default_rng(n_max)
+    bad = np.tile([-1.0, -1e-300, np.nan, -np.inf, np.inf], 40)
+    good = np.exp(rng.uniform(-10, 8, 300))
+    x = np.concatenate([bad, good])
+    perm = rng.permutation(x.size)
+    x = x[perm]
+    out = lib.boys(torch.from_numpy(x).cuda(), n_max, two_point=two_point).cpu().numpy()
+    neg_or_nan = np.isnan(x) | (x < 0)
+    assert np.all(np.isnan(out[neg_or_nan]))
+    assert np.all(out[x == np.inf] == 0.0)
+    fin = np.isfinite(x) & (x >= 0)
+    assert np.all(np.isfinite(out[fin]))
+
+
 @pytest.mark.parametrize("count", [0, 1, 2, 3, 31, 33, 127, 128, 129, 255, 257, 65537])
 def test_tail_sizes(lib, oracle_mod, count):
     import torch
