@@ -110,8 +110,9 @@ def test_special_arguments(lib, oracle_mod):
         got, xf = _gpu(lib, x, n_max)
         rel = _check(got, oracle_mod.boys(xf.astype(np.float64), n_max))
         assert rel.max() <= TOL, (n_max, xf[np.argmax(rel.max(axis=1))])
-    bad, _ = _gpu(lib, np.array([-1.0, -1e-30, np.nan, -np.inf, np.inf], dtype=np.float32), 8)
-    assert np.all(np.isnan(bad[:4])) and np.all(bad[4] == 0.0)
+    for n_max in (8, 16):  # both tile shapes
+        bad, _ = _gpu(lib, np.array([-1.0, -1e-30, np.nan, -np.inf, np.inf], dtype=np.float32), n_max)
+        assert np.all(np.isnan(bad[:4])) and np.all(bad[4] == 0.0)
 
 
 @pytest.mark.parametrize("count", [1, 2, 3, 31, 33, 255, 2047, 2048, 2049, 65537])
