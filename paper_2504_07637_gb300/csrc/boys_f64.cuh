@@ -25,12 +25,16 @@
 #include "boys_coeffs_f64.inc"
 #include "boys_common.cuh"
 
+#include <climits>
 #include <type_traits>
 
 namespace boys {
 
 // 2^(j/64), j = 0..63, for the exponential below
 static __constant__ double kExp2Frac64[64] = BOYS_EXP2_FRAC64;
+
+// Row index of a lane without a list entry (rows of carried entries may be negative).
+constexpr int kNoRow = INT_MIN;
 
 static_assert(f64_top_order(kMaxNF64) <= BOYS_F64_TABLE_MAX_N, "fitted table too short");
 
@@ -179,7 +183,7 @@ __device__ __forceinline__ int shfl_idx_volatile(int v, int src) {
 }
 
 // Write columns m0 .. m0 + LEN - 1 of the warp's staged rows: row 32 k + l
-// is entry k (row index j[k]) of lane l; j[k] < 0 marks a lane without one.
+// is entry k (row index j[k]) of lane l; j[k] == kNoRow marks a lane without one.
 template <int W, int CH, int K, int LEN>
 __device__ __forceinline__ void f64_stage_flush(double *__restrict__ out, const double *__restrict__ stg, int m0,
                                                 const int (&j)[K], int lane) {
@@ -189,7 +193,7 @@ __device__ __forceinline__ void f64_stage_flush(double *__restrict__ out, const 
     const int f = 32 * t + lane;
     const int r = f / LEN, e = f - r * LEN;
     const int jr = shfl_idx_volatile(j[t / LEN], r & 31);
-    if (jr >= 0) __stcs(out + ((int64_t)jr * W + (m0 + e)), stg[r * F64Stage<CH, K>::kPitch + e]);
+    if (jr != kNoRow) __stcs(out + ((int64_t)jr * W + (m0 + e)), stg[r * F64Stage<CH, K>::kPitch + e]);
   }
   __syncwarp();
 }
@@ -325,8 +329,22 @@ struct ContractDot {
   }
 };
 
-template <int TILE>
-struct F64TileSmem {
+// Entries of each list carried into the block's next tile (fewer than one
+// warp request): argument and row, the row relative to that tile's first
+// argument.  Without carrying only the (zero) counts exist.
+template <bool CARRY>
+struct F64Carry {
+  double cx[2][64];
+  int cj[2][64];
+  int cn[2];
+};
+template <>
+struct F64Carry<false> {
+  int cn[2];
+};
+
+template <int TILE, bool CARRY = false>
+struct F64TileSmem : F64Carry<CARRY> {
   double xs[TILE];
   unsigned short lst[TILE];  // below list from the front, above list from the back
   double tab64[64];
@@ -341,9 +359,10 @@ struct F64TileSmem {
 // ALLOW_ILP = false keeps one list entry per lane at every order (a kernel
 // that switches between orders keeps the register count of the smallest).
 template <int NMAX, int BLOCK, int TILE, typename Epi, bool TWO = false, bool ALLOW_ILP = true, int STAGE = 0,
-          int STAGE_K = 2>
+          int STAGE_K = 2, bool CARRY = false>
 __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel, const Epi &epi,
-                                         F64TileSmem<TILE> &sm, double *__restrict__ stage = nullptr) {
+                                         F64TileSmem<TILE, CARRY> &sm, double *__restrict__ stage = nullptr,
+                                         bool last = true) {
   constexpr int NTOP = f64_top_order(NMAX);
   constexpr int W = NMAX + 1;
   static_assert(TILE % BLOCK == 0 && TILE <= 65536, "tile");
@@ -384,22 +403,50 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
   constexpr bool STAGED = STAGE > 0;
   static_assert(!STAGED || Epi::kRowStore, "staging serves row stores");
   constexpr int ILP = STAGED ? STAGE_K : ((NMAX >= 12 && !TWO && ALLOW_ILP) ? 2 : 1);
+  constexpr int CHUNK = 32 * ILP;  // entries per warp request
+  static_assert(!CARRY || (CHUNK <= 64 && BLOCK >= 2 * CHUNK), "carry arrays");
   using Stage = F64Stage<(STAGED ? STAGE : 1), ILP>;
   double *const stg = STAGED ? stage + (threadIdx.x >> 5) * Stage::kDoublesPerWarp : nullptr;
+  // CARRY: the entries carried from the block's previous tile come first in
+  // each list, and a list evaluates only whole warp requests, carrying the
+  // rest into the next tile (a partly filled request costs the FP64 pipe as
+  // much as a full one), unless this is the block's last tile or the list
+  // holds less than one request.  Carried entries are thus evaluated exactly
+  // one tile later.
+  const int clo = CARRY ? sm.cn[0] : 0, chi = CARRY ? sm.cn[1] : 0;
+  const int tlo = clo + nlo, thi = chi + nhi;
+  const int flo = (CARRY && !last && tlo >= CHUNK) ? tlo / CHUNK * CHUNK : tlo;
+  const int fhi = (CARRY && !last && thi >= CHUNK) ? thi / CHUNK * CHUNK : thi;
+  // entry q of list L (0 below, 1 above): its argument, and its row relative
+  // to this tile's first argument
+  auto entry = [&](const int L, const int q, double &x) -> int {
+    const int c = L ? chi : clo;
+    if constexpr (CARRY) {
+      if (q < c) {
+        x = sm.cx[L][q];
+        return sm.cj[L][q];
+      }
+    }
+    const int i = q - c;
+    const int j = L ? sm.lst[TILE - 1 - i] : sm.lst[i];
+    x = sm.xs[j];
+    return j;
+  };
   for (;;) {
     int c = 0;
-    if (lane == 0) c = atomicAdd(&sm.next[0], 32 * ILP);
+    if (lane == 0) c = atomicAdd(&sm.next[0], CHUNK);
     c = __shfl_sync(0xffffffffu, c, 0);
-    if (c >= nlo) break;
+    if (c >= flo) break;
     const int q = c + lane;
     if constexpr (STAGED) {
       // the whole warp takes part; lanes past the end of the list compute a
       // dummy argument and store nothing (with 32 entries or fewer left, one
       // entry per lane)
       if constexpr (ILP == 2) {
-        if (nlo - c <= 32) {
-          const int j1[1] = {q < nlo ? (int)sm.lst[q] : -1};
-          const double x1[1] = {j1[0] >= 0 ? sm.xs[j1[0]] : 1.0};
+        if (flo - c <= 32) {
+          double x1[1] = {1.0};
+          int j1[1] = {kNoRow};
+          if (q < flo) j1[0] = entry(0, q, x1[0]);
           f64_formula_staged<NTOP, NMAX, STAGE, 1, TWO>(x1, j1, epi.out, stg, sm.tab64, lane);
           continue;
         }
@@ -408,31 +455,34 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
       double xv[ILP];
 #pragma unroll
       for (int k = 0; k < ILP; ++k) {
-        j[k] = q + 32 * k < nlo ? (int)sm.lst[q + 32 * k] : -1;
-        xv[k] = j[k] >= 0 ? sm.xs[j[k]] : 1.0;
+        xv[k] = 1.0;
+        j[k] = kNoRow;
+        if (q + 32 * k < flo) j[k] = entry(0, q + 32 * k, xv[k]);
       }
       f64_formula_staged<NTOP, NMAX, STAGE, ILP, TWO>(xv, j, epi.out, stg, sm.tab64, lane);
       continue;
     }
     if constexpr (ILP == 2) {
-      if (q + 32 < nlo) {
-        const int ja = sm.lst[q], jb = sm.lst[q + 32];
+      if (q + 32 < flo) {
+        double xa, xb;
+        const int ja = entry(0, q, xa), jb = entry(0, q + 32, xb);
         double Fa[W], Fb[W];
-        f64_formula<NTOP, NMAX>(sm.xs[ja], Fa, sm.tab64);
-        f64_formula<NTOP, NMAX>(sm.xs[jb], Fb, sm.tab64);
+        f64_formula<NTOP, NMAX>(xa, Fa, sm.tab64);
+        f64_formula<NTOP, NMAX>(xb, Fb, sm.tab64);
         epi(ja, Fa);
         epi(jb, Fb);
         continue;
       }
     }
-    if (q < nlo) {
-      const int j = sm.lst[q];
+    if (q < flo) {
+      double xq;
+      const int j = entry(0, q, xq);
       double F[W];
       if constexpr (TWO) {
         constexpr int NBAR = f64_two_point_nbar(NMAX);
-        f64_formula_two<NTOP, f64_top_order(NBAR), NBAR, NMAX>(sm.xs[j], F, sm.tab64);
+        f64_formula_two<NTOP, f64_top_order(NBAR), NBAR, NMAX>(xq, F, sm.tab64);
       } else {
-        f64_formula<NTOP, NMAX>(sm.xs[j], F, sm.tab64);
+        f64_formula<NTOP, NMAX>(xq, F, sm.tab64);
       }
       epi(j, F);
     }
@@ -441,15 +491,16 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
   // orders, as above: the upward product chain is 2 n_max long)
   for (;;) {
     int c = 0;
-    if (lane == 0) c = atomicAdd(&sm.next[1], 32 * ILP);
+    if (lane == 0) c = atomicAdd(&sm.next[1], CHUNK);
     c = __shfl_sync(0xffffffffu, c, 0);
-    if (c >= nhi) break;
+    if (c >= fhi) break;
     const int q = c + lane;
     if constexpr (STAGED) {
       if constexpr (ILP == 2) {
-        if (nhi - c <= 32) {
-          const int j1[1] = {q < nhi ? (int)sm.lst[TILE - 1 - q] : -1};
-          const double x1[1] = {j1[0] >= 0 ? sm.xs[j1[0]] : 1.0};
+        if (fhi - c <= 32) {
+          double x1[1] = {1.0};
+          int j1[1] = {kNoRow};
+          if (q < fhi) j1[0] = entry(1, q, x1[0]);
           f64_asymptote_staged<NMAX, STAGE, 1>(x1, j1, epi.out, stg, lane);
           continue;
         }
@@ -458,36 +509,61 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
       double xv[ILP];
 #pragma unroll
       for (int k = 0; k < ILP; ++k) {
-        j[k] = q + 32 * k < nhi ? (int)sm.lst[TILE - 1 - (q + 32 * k)] : -1;
-        xv[k] = j[k] >= 0 ? sm.xs[j[k]] : 1.0;
+        xv[k] = 1.0;
+        j[k] = kNoRow;
+        if (q + 32 * k < fhi) j[k] = entry(1, q + 32 * k, xv[k]);
       }
       f64_asymptote_staged<NMAX, STAGE, ILP>(xv, j, epi.out, stg, lane);
       continue;
     }
     if constexpr (ILP == 2) {
-      if (q + 32 < nhi) {
-        const int ja = sm.lst[TILE - 1 - q], jb = sm.lst[TILE - 1 - (q + 32)];
+      if (q + 32 < fhi) {
+        double xa, xb;
+        const int ja = entry(1, q, xa), jb = entry(1, q + 32, xb);
         double Fa[W], Fb[W];
-        f64_asymptote<NMAX>(sm.xs[ja], Fa);
-        f64_asymptote<NMAX>(sm.xs[jb], Fb);
+        f64_asymptote<NMAX>(xa, Fa);
+        f64_asymptote<NMAX>(xb, Fb);
         epi(ja, Fa);
         epi(jb, Fb);
         continue;
       }
     }
-    if (q < nhi) {
-      const int j = sm.lst[TILE - 1 - q];
+    if (q < fhi) {
+      double xq;
+      const int j = entry(1, q, xq);
       double F[W];
-      f64_asymptote<NMAX>(sm.xs[j], F);
+      f64_asymptote<NMAX>(xq, F);
       epi(j, F);
     }
   }
   __syncthreads();
+  if constexpr (CARRY) {
+    if (!last) {
+      // the rest of each list (fewer than CHUNK entries, all from this tile's
+      // list since the carried ones came first) moves to the carry, its rows
+      // made relative to the block's next tile
+      const int rlo = tlo - flo, rhi = thi - fhi;
+      const int shift = (int)gridDim.x * TILE;
+      if (threadIdx.x < rlo + rhi) {
+        const int L = threadIdx.x < rlo ? 0 : 1;
+        const int p = L ? threadIdx.x - rlo : threadIdx.x;
+        double x;
+        const int j = entry(L, (L ? fhi : flo) + p, x);
+        sm.cx[L][p] = x;
+        sm.cj[L][p] = j - shift;
+      }
+      if (threadIdx.x == 0) {
+        sm.cn[0] = rlo;
+        sm.cn[1] = rhi;
+      }
+    }
+  }
 }
 
-template <int BLOCK, int TILE>
-__device__ __forceinline__ void f64_load_table(F64TileSmem<TILE> &sm) {
+template <int BLOCK, typename Smem>
+__device__ __forceinline__ void f64_load_table(Smem &sm) {
   for (int i = threadIdx.x; i < 64; i += BLOCK) sm.tab64[i] = kExp2Frac64[i];
+  if (threadIdx.x == 0) sm.cn[0] = sm.cn[1] = 0;  // nothing carried yet
 }
 
 template <int BLOCK, int STAGE, int K>
@@ -501,7 +577,7 @@ constexpr size_t f64_stage_bytes() {
 template <int BLOCK, int TILE, int STAGE, int K>
 constexpr int f64_min_blocks() {
   if (STAGE == 0) return 1;
-  const size_t per_block = sizeof(F64TileSmem<TILE>) + f64_stage_bytes<BLOCK, STAGE, K>() + 1024;
+  const size_t per_block = sizeof(F64TileSmem<TILE, true>) + f64_stage_bytes<BLOCK, STAGE, K>() + 1024;
   const int b = (int)((size_t)228 * 1024 / per_block);
   return b < 1 ? 1 : (b > 4 ? 4 : b);
 }
@@ -509,13 +585,14 @@ constexpr int f64_min_blocks() {
 // Tiles of a persistent block (all kernels below).
 template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO, int STAGE, int K>
 __device__ __forceinline__ void f64_tiles(const double *__restrict__ x, int64_t count, const MakeEpi &make,
-                                          F64TileSmem<TILE> &sm, double *__restrict__ stage) {
-  f64_load_table<BLOCK, TILE>(sm);
+                                          F64TileSmem<TILE, true> &sm, double *__restrict__ stage) {
+  f64_load_table<BLOCK>(sm);
   const int64_t ntiles = (count + TILE - 1) / TILE;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t base = t * TILE;
     const int nel = (int)((count - base) < TILE ? (count - base) : TILE);
-    f64_tile<NMAX, BLOCK, TILE, decltype(make(base)), TWO, true, STAGE, K>(x + base, nel, make(base), sm, stage);
+    f64_tile<NMAX, BLOCK, TILE, decltype(make(base)), TWO, true, STAGE, K, true>(x + base, nel, make(base), sm, stage,
+                                                                              t + gridDim.x >= ntiles);
   }
 }
 
@@ -523,7 +600,7 @@ __device__ __forceinline__ void f64_tiles(const double *__restrict__ x, int64_t 
 template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO = false>
 __global__ void __launch_bounds__(BLOCK) f64_split_kernel(const double *__restrict__ x, int64_t count,
                                                           const MakeEpi make) {
-  __shared__ F64TileSmem<TILE> sm;
+  __shared__ F64TileSmem<TILE, true> sm;
   f64_tiles<NMAX, BLOCK, TILE, MakeEpi, TWO, 0, 1>(x, count, make, sm, nullptr);
 }
 
@@ -532,7 +609,7 @@ __global__ void __launch_bounds__(BLOCK) f64_split_kernel(const double *__restri
 template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO, int STAGE, int K>
 __global__ void __launch_bounds__(BLOCK, (f64_min_blocks<BLOCK, TILE, STAGE, K>()))
     f64_staged_kernel(const double *__restrict__ x, int64_t count, const MakeEpi make) {
-  __shared__ F64TileSmem<TILE> sm;
+  __shared__ F64TileSmem<TILE, true> sm;
   extern __shared__ __align__(16) unsigned char f64_stage_raw[];
   f64_tiles<NMAX, BLOCK, TILE, MakeEpi, TWO, STAGE, K>(x, count, make, sm,
                                                        reinterpret_cast<double *>(f64_stage_raw));

@@ -122,7 +122,7 @@ template <int BLOCK, int TILE>
 __global__ void __launch_bounds__(BLOCK) ragged_eval_kernel(const RaggedArgs a) {
   __shared__ RaggedSmem<BLOCK, TILE> sm;
   extern __shared__ int64_t pref_s[];  // tile prefix when it fits, else unused
-  boys::f64_load_table<BLOCK, TILE>(sm.tile);
+  boys::f64_load_table<BLOCK>(sm.tile);
   const int R = a.num_requests;
   const bool in_smem = R < kSmemPrefixMax;
   if (in_smem)
