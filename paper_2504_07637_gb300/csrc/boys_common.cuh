@@ -27,12 +27,6 @@ __device__ __forceinline__ T ipow(T a) {
   }
 }
 
-// 1/(2m-1) as a compile-time double (the downward-recursion divisor).
-template <int M>
-__device__ __forceinline__ constexpr double inv_odd() {
-  return 1.0 / double(2 * M - 1);
-}
-
 // Order evaluated for a requested n_max on the double path: computing
 // F_{n_top} with n_top > n_max and recursing down buys accuracy at m = n_max
 // (Sec. 3 suggests n_top = n_max + 1); the offsets keep every m within 2e-14
