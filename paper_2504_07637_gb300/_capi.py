@@ -94,6 +94,3 @@ def call(name: str, *args) -> None:
     if rc != 0:
         raise BoysError(name, rc)
 
-
-def exported_symbols() -> list[str]:
-    return list(SIGNATURES)
