@@ -93,6 +93,19 @@ __global__ void __launch_bounds__(F32Tile<NMAX, MODE, BLOCK_, TILE_>::BLOCK)
   float cu[W];
 #pragma unroll
   for (int m = 0; m < W; ++m) cu[m] = (MODE == 1 && cf.c_row == 0) ? __ldg(cf.c + m * cf.c_col) : 0.0f;
+  // Uniform contraction of the asymptote row: with F_m = F_0 prod_{k<=m} (k - 1/2) y
+  // (y = 1/x), sum_m c_m F_m = F_0 P(y), P(y) = sum_m hu_m y^m and
+  // hu_m = c_m prod_{k<=m} (k - 1/2): a Horner polynomial instead of the row
+  // and its dot product.
+  float hu[W];
+  {
+    float g = 1.0f;
+#pragma unroll
+    for (int m = 0; m < W; ++m) {
+      if (m > 0) g *= float(m) - 0.5f;
+      hu[m] = cu[m] * g;
+    }
+  }
   // the next tile's arguments are loaded into registers while the current
   // tile is evaluated, so the load latency hides behind the arithmetic
   float pre[PER];
@@ -122,9 +135,17 @@ __global__ void __launch_bounds__(F32Tile<NMAX, MODE, BLOCK_, TILE_>::BLOCK)
       const bool valid = j < nel;
       const bool lo = valid && below_cutoff_f32(v, zbits);
       xs[j] = v;
-      float F[W];
-      f32_asymptote<NMAX>(v, F);
-      if (MODE == 0 || valid) f32_emit<W, MODE>(rows, j, base + j, F, cf, cu);
+      if (MODE == 1 && cf.c_row == 0) {
+        const float y = boys_frcp_rn(v);
+        float acc = hu[W - 1];
+#pragma unroll
+        for (int m = W - 2; m >= 0; --m) acc = fmaf(acc, y, hu[m]);
+        if (valid) rows[j] = acc * (0.886226925452758f * boys_rsqrtf(v));
+      } else {
+        float F[W];
+        f32_asymptote<NMAX>(v, F);
+        if (MODE == 0 || valid) f32_emit<W, MODE>(rows, j, base + j, F, cf, cu);
+      }
       const unsigned mlo = __ballot_sync(0xffffffffu, lo);
       int plo = 0;
       if (lane == 0 && mlo) plo = atomicAdd(&cnt[0], __popc(mlo));
