@@ -71,8 +71,11 @@ __device__ __forceinline__ void f32_emit(float *__restrict__ rows, int j, int64_
   }
 }
 
+// The contraction (MODE 1) is bound by instruction issue: compiled for 8
+// resident blocks of 128 threads (64 registers), it keeps enough warps to
+// fill the schedulers (measured faster than 72 registers and 7 blocks).
 template <int NMAX, int MODE, int BLOCK_ = 0, int TILE_ = 0>
-__global__ void __launch_bounds__(F32Tile<NMAX, MODE, BLOCK_, TILE_>::BLOCK)
+__global__ void __launch_bounds__(F32Tile<NMAX, MODE, BLOCK_, TILE_>::BLOCK, (MODE == 1 ? 8 : 1))
     f32_split_kernel(const float *__restrict__ x, int64_t count, float *__restrict__ out, const F32Coef cf) {
   using P = F32Tile<NMAX, MODE, BLOCK_, TILE_>;
   static_assert(P::BLOCK >= 64 && P::TILE % P::BLOCK == 0 && P::TILE <= 65536, "shape");  // 64: the table load
