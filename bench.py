@@ -698,9 +698,9 @@ def measure_contract(wl, steps, warmup, device, seed, rates=None):
     if not f32 and rates is not None:
         n_top = _capi.load().boys_top_order_f64(n_max)
         fb = float(np.mean(x_host <= _capi.load().boys_cutoff(n_top, 53)))
-        below, above = roofline.f64_counts(n_max, n_top)
+        # the weights are the same for every argument (row stride 0)
+        below, above = roofline.f64_counts_contract(n_max, n_top, uniform=True)
         t_arg = sum((fb * below[k] + (1 - fb) * above[k]) / rates[k] for k in ("fma", "div", "sqrt", "exp", "rsqrt"))
-        t_arg += (n_max + 1) / rates["fma"]  # the contraction's fused multiply-adds
         res["roofline_bound"] = "alu"
         res["roofline_frac"] = round(t_arg * count / (ms / 1e3), 4)
     else:

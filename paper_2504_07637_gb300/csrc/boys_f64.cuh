@@ -291,6 +291,7 @@ __device__ __forceinline__ bool below_cutoff(double v, unsigned long long zbits)
 template <int W>
 struct StoreRows {
   static constexpr bool kRowStore = true;  // the rows may go out through the staging buffer
+  static constexpr bool kHorner = false;
   double *out;  // row 0 of the tile
   __device__ __forceinline__ void operator()(int j, const double (&F)[W]) const { store_row<W>(out + (int64_t)j * W, F); }
 };
@@ -300,6 +301,7 @@ struct StoreRows {
 template <int W>
 struct GradDot {
   static constexpr bool kRowStore = false;
+  static constexpr bool kHorner = false;
   const double *g;  // row 0 of the tile
   int64_t g_row, g_col;
   double *grad;  // element 0 of the tile
@@ -317,9 +319,16 @@ struct GradDot {
 template <int W>
 struct ContractDot {
   static constexpr bool kRowStore = false;
+  // up to n_max = 16: above, the W coefficients held in registers next to two
+  // rows per lane would cost more occupancy than the polynomial saves
+  static constexpr bool kHorner = W <= 17;
   const double *c;  // row 0 of the tile
   int64_t c_row, c_col;
   double *out;  // element 0 of the tile
+  // with the same coefficients for every argument (c_row == 0):
+  // hu_m = c_m prod_{k<=m} (k - 1/2), the asymptote's contraction as a
+  // polynomial in y = 1/x (MakeContract::prepare)
+  double hu[W];
   __device__ __forceinline__ void operator()(int j, const double (&F)[W]) const {
     const double *cj = c + (int64_t)j * c_row;
     double acc = 0.0;
@@ -327,6 +336,19 @@ struct ContractDot {
     for (int m = 0; m < W; ++m) acc = fma(__ldg(cj + m * c_col), F[m], acc);
     out[j] = acc;
   }
+  __device__ __forceinline__ bool uniform() const { return c_row == 0; }
+  // Above the cut-off, where F_m = F_0 prod_{k<=m} (k - 1/2) y: the
+  // contraction is F_0 P(y) by Horner (uniform coefficients only); the same
+  // 1/x and rsqrt forms as f64_asymptote.
+  __device__ __forceinline__ double asymptote_dot(const double x) const {
+    const double rs = rsqrt(x);
+    const double y = W - 1 <= 12 ? rs * rs : 1.0 / x;
+    double acc = hu[W - 1];
+#pragma unroll
+    for (int m = W - 2; m >= 0; --m) acc = fma(acc, y, hu[m]);
+    return acc * (0.88622692545275801365 * rs);
+  }
+  __device__ __forceinline__ void put(int j, double v) const { out[j] = v; }
 };
 
 // Entries of each list carried into the block's next tile (fewer than one
@@ -495,6 +517,19 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
     c = __shfl_sync(0xffffffffu, c, 0);
     if (c >= fhi) break;
     const int q = c + lane;
+    if constexpr (Epi::kHorner) {
+      if (epi.uniform()) {  // the contraction of the asymptote as a polynomial
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) {
+          if (q + 32 * k < fhi) {
+            double xq;
+            const int j = entry(1, q + 32 * k, xq);
+            epi.put(j, epi.asymptote_dot(xq));
+          }
+        }
+        continue;
+      }
+    }
     if constexpr (STAGED) {
       if constexpr (ILP == 2) {
         if (fhi - c <= 32) {
@@ -587,12 +622,14 @@ template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO, int STAGE, 
 __device__ __forceinline__ void f64_tiles(const double *__restrict__ x, int64_t count, const MakeEpi &make,
                                           F64TileSmem<TILE, true> &sm, double *__restrict__ stage) {
   f64_load_table<BLOCK>(sm);
+  MakeEpi mk = make;
+  mk.prepare();
   const int64_t ntiles = (count + TILE - 1) / TILE;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t base = t * TILE;
     const int nel = (int)((count - base) < TILE ? (count - base) : TILE);
-    f64_tile<NMAX, BLOCK, TILE, decltype(make(base)), TWO, true, STAGE, K, true>(x + base, nel, make(base), sm, stage,
-                                                                              t + gridDim.x >= ntiles);
+    f64_tile<NMAX, BLOCK, TILE, decltype(mk(base)), TWO, true, STAGE, K, true>(x + base, nel, mk(base), sm, stage,
+                                                                            t + gridDim.x >= ntiles);
   }
 }
 
@@ -618,6 +655,7 @@ __global__ void __launch_bounds__(BLOCK, (f64_min_blocks<BLOCK, TILE, STAGE, K>(
 template <int W>
 struct MakeStore {
   double *out;
+  __device__ __forceinline__ void prepare() {}
   __device__ __forceinline__ StoreRows<W> operator()(int64_t base) const { return StoreRows<W>{out + base * W}; }
 };
 
@@ -626,6 +664,7 @@ struct MakeGrad {
   const double *g;
   int64_t g_row, g_col;
   double *grad;
+  __device__ __forceinline__ void prepare() {}
   __device__ __forceinline__ GradDot<W> operator()(int64_t base) const {
     return GradDot<W>{g + base * g_row, g_row, g_col, grad + base};
   }
@@ -636,8 +675,21 @@ struct MakeContract {
   const double *c;
   int64_t c_row, c_col;
   double *out;
+  double hu[W];  // filled by prepare() on the device
+  // once per thread: the Horner coefficients of the asymptote's contraction
+  __device__ __forceinline__ void prepare() {
+    double g = 1.0;
+#pragma unroll
+    for (int m = 0; m < W; ++m) {
+      if (m > 0) g *= double(m) - 0.5;
+      hu[m] = (ContractDot<W>::kHorner && c_row == 0) ? __ldg(c + m * c_col) * g : 0.0;
+    }
+  }
   __device__ __forceinline__ ContractDot<W> operator()(int64_t base) const {
-    return ContractDot<W>{c + base * c_row, c_row, c_col, out + base};
+    ContractDot<W> d{c + base * c_row, c_row, c_col, out + base, {}};
+#pragma unroll
+    for (int m = 0; m < W; ++m) d.hu[m] = hu[m];
+    return d;
   }
 };
 

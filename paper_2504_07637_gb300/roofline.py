@@ -93,5 +93,24 @@ def f64_counts_two_point(n_max: int, n_top: int, n_bar: int, n_top_lo: int) -> t
     return below, _asymptote_counts(n_max)
 
 
+def f64_counts_contract(n_max: int, n_top: int, uniform: bool = True) -> tuple[dict, dict]:
+    """As f64_counts for the fused contraction sum_m c_m F_m: below the
+    cut-off the row as f64_counts plus the n_max + 1 term dot product; above
+    it, with the same coefficients for every argument and n_max <= 16, the
+    contraction of the asymptote as a polynomial in y = 1/x (Horner, n_max
+    fused multiply-adds, y and two products), else the asymptote row and the
+    dot product."""
+    below, above = f64_counts(n_max, n_top)
+    below["fma"] += n_max + 1
+    if uniform and n_max <= 16:
+        # y = rs^2 (n_max <= 12) or 1/x, needed only from n_max = 1 on
+        above = {"fma": (1 if 1 <= n_max <= 12 else 0) + n_max + 2, "div": 1 if n_max > 12 else 0, "sqrt": 0,
+                 "exp": 0, "rsqrt": 1}
+    else:
+        above = dict(above)
+        above["fma"] += n_max + 1
+    return below, above
+
+
 def bytes_per_arg(n_max: int, elem: int = 8) -> int:
     return elem * (1 + n_max + 1)

@@ -63,3 +63,16 @@ def test_two_point_is_two_closed_forms_and_two_recursions():
     # each one-point count holds its full recursion (2 n_top); the two-point
     # recursions run n_top -> n_bar + 1 and n_top_lo -> 0
     assert two["fma"] == (one["fma"] - 2 * n_top) + (lo["fma"] - 2 * n_top_lo) + 2 * (n_top - n_bar - 1) + 2 * n_top_lo
+
+
+def test_contraction_counts():
+    # below the cut-off: the row plus an (n_max + 1)-term dot product; above it
+    # with uniform weights: Horner in y = 1/x (y = rs^2 up to n_max = 12)
+    for n_max, n_top in ((0, 0), (8, 9), (16, 18)):
+        row_b, row_a = roofline.f64_counts(n_max, n_top)
+        b, a = roofline.f64_counts_contract(n_max, n_top, uniform=True)
+        assert b["fma"] == row_b["fma"] + n_max + 1 and b["exp"] == 1
+        assert a["fma"] == n_max + 2 + (1 if 1 <= n_max <= 12 else 0) and a["rsqrt"] == 1
+        assert a["fma"] < row_a["fma"] + n_max + 1  # cheaper than the row and its dot product
+    b, a = roofline.f64_counts_contract(36, 40, uniform=True)  # no Horner above n_max = 16
+    assert a["fma"] == roofline.f64_counts(36, 40)[1]["fma"] + 37
