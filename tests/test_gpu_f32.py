@@ -6,6 +6,7 @@ normal float (>= FLT_MIN); below that, |out - exact| <= 2e-6 |exact| + one
 subnormal unit (2^-149): a float cannot carry more there.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -149,10 +150,10 @@ def test_full_size_scale_workload_sampled(lib, oracle_mod, record_property):
 
     xf = workloads.scale(1 << 26).astype(np.float32)
     out = lib.boys(torch.from_numpy(xf).cuda(), 8)
-    idx = np.sort(np.random.default_rng(8).choice(xf.size, 1 << 16, replace=False))
+    idx = np.sort(np.random.default_rng(8).choice(xf.size, 1 << 20, replace=False))  # a 2^20 sample
     idx = np.concatenate([idx, [0, xf.size - 1]])
     got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
-    rel = _check(got, oracle_mod.boys(xf[idx].astype(np.float64), 8))
+    rel = _check(got, oracle_mod.boys_threaded(xf[idx].astype(np.float64), 8, os.cpu_count() or 1))
     record_property("max_rel_err_per_m", _per_m(rel))
     assert rel.max() <= TOL
     del out

@@ -4,6 +4,7 @@ Tolerance: max relative error 2e-14 for every m (the double-path target);
 rows with a NaN or zero reference are compared exactly.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -202,10 +203,10 @@ def test_full_size_scale_workload_sampled(lib, oracle_mod, n_max, record_propert
     x = workloads.scale(1 << 26)
     xd = torch.from_numpy(x).cuda()
     out = lib.boys(xd, n_max)
-    idx = np.sort(np.random.default_rng(n_max).choice(x.size, 1 << 15, replace=False))
+    idx = np.sort(np.random.default_rng(n_max).choice(x.size, 1 << 20, replace=False))  # a 2^20 sample
     idx = np.concatenate([idx, [0, x.size - 1]])
     got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
-    ref = oracle_mod.boys(x[idx], n_max)
+    ref = oracle_mod.boys_threaded(x[idx], n_max, os.cpu_count() or 1)
     rel = _relerr(got, ref)
     record_property("max_rel_err_per_m", _per_m(rel))
     assert rel.max() <= TOL
