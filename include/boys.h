@@ -125,7 +125,11 @@ boys_status boys_eval_f64_two_point(const double *x, int64_t count, int n_max, d
  *        coefficient vector over all arguments)
  *   out: device, [count]
  * Same method and per-F_m accuracy as boys_eval_f64 / boys_eval_f32; the
- * contraction itself rounds in the working precision. */
+ * contraction itself rounds in the working precision.  With one coefficient
+ * vector for all arguments (c_row == 0; FP64 up to n_max = 16), arguments
+ * above the cut-off take the contraction of the asymptote as a polynomial
+ * in 1/x (Horner), without forming the row: the result differs from
+ * contracting the rows by rounding only (a few ulp of sum_m |c_m| F_m). */
 boys_status boys_eval_contract_f64(const double *x, int64_t count, int n_max, const double *c, int64_t c_row,
                                    int64_t c_col, double *out, void *stream);
 boys_status boys_eval_contract_f32(const float *x, int64_t count, int n_max, const float *c, int64_t c_row,
