@@ -509,6 +509,16 @@ def run_grad(args, wl, emit=True):
     F = boys.boys(xd, n_max + 1)
     fwd = _events_ms(lambda: boys.boys(xd, n_max + 1, out=F), stream, 10)
     bwd = _events_ms(lambda: boys.boys_backward(xd, gw, n_max, F), stream, 10)
+    # the backward's device time: calls queued back to back, so the host's
+    # ~30 us per call (wrapper, checks, launch) overlaps the previous kernel
+    torch.cuda.synchronize()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for _ in range(20):
+        boys.boys_backward(xd, gw, n_max, F)
+    q1.record(stream)
+    q1.synchronize()
+    bwd_queued_ms = q0.elapsed_time(q1) / 20
     # central differences would need two forwards of n_max (the method's own alternative)
     fwd8 = _events_ms(lambda: boys.boys(xd, n_max), stream, 10)
     bwd_ms = statistics.median(bwd)
@@ -533,17 +543,18 @@ def run_grad(args, wl, emit=True):
                    "max_rel_err_grad": 1e-12},
         "forward_ms": round(statistics.median(fwd), 4),
         "backward_ms": round(bwd_ms, 4),
+        "backward_ms_queued": round(bwd_queued_ms, 4),
         "central_difference_ms": round(2 * statistics.median(fwd8), 4),
         "backward_speedup_vs_central_difference": round(2 * statistics.median(fwd8) / bwd_ms, 2),
         "clocks": clk,
         "gpu_launches": 2 * args.steps,
-        "roofline": {"bound": "alu", "achieved": round(count * (n_max + 1) / (bwd_ms / 1e3) / 1e12, 5),
+        "roofline": {"bound": "alu", "achieved": round(count * (n_max + 1) / (bwd_queued_ms / 1e3) / 1e12, 5),
                      "peak": round(rates["fma"] / 1e12, 5), "unit": "TFLOP/s",
-                     "frac": round(count * (n_max + 1) / (bwd_ms / 1e3) / rates["fma"], 4),
+                     "frac": round(count * (n_max + 1) / (bwd_queued_ms / 1e3) / rates["fma"], 4),
                      "traffic": traffic_record("grad_saved_kernel<8>/differentiation_2^24"),
-                     "note": f"backward kernel: n_max+1 FP64 fma per argument vs the measured DFMA rate; HBM side "
-                     f"{bwd_bytes / (bwd_ms / 1e3) / 1e9:.0f} GB/s of {hbm_peak:.0f} ({src}) for "
-                     f"{8 * (n_max + 2)} algorithmic bytes per argument"},
+                     "note": f"backward kernel (device time, calls queued): n_max+1 FP64 fma per argument vs the "
+                     f"measured DFMA rate; HBM side {bwd_bytes / (bwd_queued_ms / 1e3) / 1e9:.0f} GB/s of "
+                     f"{hbm_peak:.0f} ({src}) for {8 * (n_max + 2)} algorithmic bytes per argument"},
     }
     if emit:
         print(json.dumps(line), flush=True)
@@ -864,7 +875,7 @@ def main():
         suite["ragged_f64"]["variant"] = rg["config"]["variant"]
         gr = run_grad(sub, WORKLOADS["grad_f64"], emit=False)
         suite["grad_f64"] = {k: gr[k] for k in ("value", "unit", "ms_per_step", "forward_ms", "backward_ms",
-                                                "backward_speedup_vs_central_difference")}
+                                                "backward_ms_queued", "backward_speedup_vs_central_difference")}
         suite["grad_f64"]["backward_roofline"] = gr["roofline"]
         extras["workloads"] = suite
     if rank == 0 and not args.no_cpu_baseline:
