@@ -703,7 +703,15 @@ def measure_contract(wl, steps, warmup, device, seed, rates=None):
     f = lambda: _capi.call(fn, x.data_ptr(), count, n_max, w.data_ptr(), 0, 1, out.data_ptr(), stream.cuda_stream)
     for _ in range(max(warmup, 3)):
         f()
-    ms = statistics.median(_events_ms(f, stream, steps))
+    # `steps` calls queued back to back between one pair of events (device time per call)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        f()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
     res = {"value": round(count * (n_max + 1) / (ms / 1e3) / 1e9, 4), "unit": "G F_m values/s (consumed)",
            "ms_per_step": round(ms, 4), "bytes_per_arg": 2 * esz}
     if not f32 and rates is not None:
