@@ -519,6 +519,13 @@ def run_grad(args, wl, emit=True):
     q1.record(stream)
     q1.synchronize()
     bwd_queued_ms = q0.elapsed_time(q1) / 20
+    # the backward without saved rows (recomputed in the kernel), device time
+    q0.record(stream)
+    for _ in range(5):
+        boys.boys_backward(xd, gw, n_max, None)
+    q1.record(stream)
+    q1.synchronize()
+    bwd_recompute_ms = q0.elapsed_time(q1) / 5
     # central differences would need two forwards of n_max (the method's own alternative)
     fwd8 = _events_ms(lambda: boys.boys(xd, n_max), stream, 10)
     bwd_ms = statistics.median(bwd)
@@ -544,6 +551,7 @@ def run_grad(args, wl, emit=True):
         "forward_ms": round(statistics.median(fwd), 4),
         "backward_ms": round(bwd_ms, 4),
         "backward_ms_queued": round(bwd_queued_ms, 4),
+        "backward_recompute_ms_queued": round(bwd_recompute_ms, 4),
         "central_difference_ms": round(2 * statistics.median(fwd8), 4),
         "backward_speedup_vs_central_difference": round(2 * statistics.median(fwd8) / bwd_ms, 2),
         "clocks": clk,
@@ -883,7 +891,8 @@ def main():
         suite["ragged_f64"]["variant"] = rg["config"]["variant"]
         gr = run_grad(sub, WORKLOADS["grad_f64"], emit=False)
         suite["grad_f64"] = {k: gr[k] for k in ("value", "unit", "ms_per_step", "forward_ms", "backward_ms",
-                                                "backward_ms_queued", "backward_speedup_vs_central_difference")}
+                                                "backward_ms_queued", "backward_recompute_ms_queued",
+                                                "backward_speedup_vs_central_difference")}
         suite["grad_f64"]["backward_roofline"] = gr["roofline"]
         extras["workloads"] = suite
     if rank == 0 and not args.no_cpu_baseline:

@@ -301,10 +301,14 @@ struct StoreRows {
 template <int W>
 struct GradDot {
   static constexpr bool kRowStore = false;
-  static constexpr bool kHorner = false;
+  // as for ContractDot (the forward order here is one above the gradient's)
+  static constexpr bool kHorner = W <= 18;
   const double *g;  // row 0 of the tile
   int64_t g_row, g_col;
   double *grad;  // element 0 of the tile
+  // with the same weights for every argument (g_row == 0):
+  // hu_m = g_m prod_{k<=m+1} (k - 1/2), m = 0..W-2 (MakeGrad::prepare)
+  double hu[W];
   __device__ __forceinline__ void operator()(int j, const double (&F)[W]) const {
     const double *gj = g + (int64_t)j * g_row;
     double acc = 0.0;
@@ -312,6 +316,19 @@ struct GradDot {
     for (int m = 0; m + 1 < W; ++m) acc = fma(__ldg(gj + m * g_col), F[m + 1], acc);
     grad[j] = -acc;
   }
+  __device__ __forceinline__ bool uniform() const { return g_row == 0; }
+  // Above the cut-off F_{m+1} = F_0 prod_{k<=m+1} (k - 1/2) y^{m+1}, so the
+  // gradient is -F_0 y P(y) by Horner (uniform weights only); the same 1/x
+  // and rsqrt forms as f64_asymptote.
+  __device__ __forceinline__ double asymptote_dot(const double x) const {
+    const double rs = rsqrt(x);
+    const double y = W - 1 <= 12 ? rs * rs : 1.0 / x;
+    double acc = hu[W - 2];
+#pragma unroll
+    for (int m = W - 3; m >= 0; --m) acc = fma(acc, y, hu[m]);
+    return -(acc * ((0.88622692545275801365 * rs) * y));
+  }
+  __device__ __forceinline__ void put(int j, double v) const { grad[j] = v; }
 };
 
 // Contraction epilogue (a fused consumer): out[j] = sum_{m=0}^{W-1} c[j, m] F_m(x_j),
@@ -664,9 +681,22 @@ struct MakeGrad {
   const double *g;
   int64_t g_row, g_col;
   double *grad;
-  __device__ __forceinline__ void prepare() {}
+  double hu[W];  // filled by prepare() on the device
+  // once per thread: the Horner coefficients of the asymptote's gradient
+  __device__ __forceinline__ void prepare() {
+    double p = 1.0;
+#pragma unroll
+    for (int m = 0; m + 1 < W; ++m) {
+      p *= double(m + 1) - 0.5;
+      hu[m] = (GradDot<W>::kHorner && g_row == 0) ? __ldg(g + m * g_col) * p : 0.0;
+    }
+    hu[W - 1] = 0.0;
+  }
   __device__ __forceinline__ GradDot<W> operator()(int64_t base) const {
-    return GradDot<W>{g + base * g_row, g_row, g_col, grad + base};
+    GradDot<W> d{g + base * g_row, g_row, g_col, grad + base, {}};
+#pragma unroll
+    for (int m = 0; m < W; ++m) d.hu[m] = hu[m];
+    return d;
   }
 };
 

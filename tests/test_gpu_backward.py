@@ -54,14 +54,41 @@ def test_against_oracle(lib, oracle_mod, n_max, mode):
 
 
 def test_recompute_equals_saved_bitwise(lib):
+    # per-argument weights: the recompute path builds every row, so both
+    # paths sum the same products in the same order
     import torch
 
     x = torch.from_numpy(_x(20000, 3)).cuda()
     w = torch.randn(9, dtype=torch.float64, device="cuda")
-    g = w.expand(x.numel(), 9)  # broadcast: row stride 0
+    g = w.expand(x.numel(), 9).contiguous()
     a = lib.boys_backward(x, g, 8, lib.boys(x, 9))
     b = lib.boys_backward(x, g, 8, None)
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("n_max", [0, 1, 8, 16, 20])
+def test_recompute_with_broadcast_weights(lib, oracle_mod, n_max):
+    # one weight vector for all arguments (row stride 0): above the cut-off the
+    # recompute path takes the gradient of the asymptote as a polynomial in
+    # 1/x (up to n_max = 16); against the oracle, and against the saved rows
+    # within a few ulp of the weighted magnitude
+    import torch
+
+    x = _x(6000, 40 + n_max)
+    w = np.random.default_rng(n_max).standard_normal(n_max + 1)
+    xd = torch.from_numpy(x).cuda()
+    g = torch.from_numpy(w).cuda().expand(x.size, n_max + 1)
+    got = lib.boys_backward(xd, g, n_max, None).cpu().numpy()
+    want, scale = _ref(oracle_mod, x, np.broadcast_to(w, (x.size, n_max + 1)).copy(), n_max)
+    err = np.abs(got - want) / np.where(scale > 0, scale, 1.0)
+    assert err.max() <= TOL, err.max()
+    saved = lib.boys_backward(xd, g, n_max, lib.boys(xd, n_max + 1)).cpu().numpy()
+    assert (np.abs(got - saved) / np.where(scale > 0, scale, 1.0)).max() <= 4e-15
+    # domain convention through the polynomial: negative or NaN x -> NaN, +inf -> 0
+    bad = torch.tensor([-1.0, float("nan"), float("inf")] * 40, dtype=torch.float64, device="cuda")
+    gb = torch.from_numpy(w).cuda().expand(bad.numel(), n_max + 1)
+    out = lib.boys_backward(bad, gb, n_max, None).cpu().numpy().reshape(40, 3)
+    assert np.all(np.isnan(out[:, :2])) and np.all(out[:, 2] == 0.0)
 
 
 def test_autograd_function_matches_oracle(lib, oracle_mod):
