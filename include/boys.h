@@ -102,7 +102,10 @@ boys_status boys_eval_f32(const float *x, int64_t count, int n_max, float *out, 
  *            vector shared by all rows)
  *   grad_x:  device, [count] doubles (overwritten)
  * n_max <= boys_max_n(53) - 1.  Relative error, normalised by
- * sum_m |g[i,m]| F_{m+1}(x_i): 1e-12. */
+ * sum_m |g[i,m]| F_{m+1}(x_i): 1e-12.  Without F and with one weight vector
+ * for all arguments (g_row_stride == 0, n_max <= 16), arguments above the
+ * cut-off take the gradient of the asymptote as a polynomial in 1/x (Horner);
+ * it differs from the saved-rows result by rounding only. */
 boys_status boys_eval_backward_f64(const double *x, const double *F, int64_t ld_F, const double *g, int64_t g_row_stride,
                                    int64_t g_col_stride, int64_t count, int n_max, double *grad_x, void *stream);
 
