@@ -204,3 +204,21 @@ def test_root_form_beats_expanded_coefficients(n):
         worst_r = max(worst_r, abs(float((roots_form(rec["u"], x) / roots_form(rec["v"], x) - exact) / exact)))
     assert worst_r < 4e-15
     assert worst_h > 10 * worst_r, (worst_h, worst_r)
+
+
+@pytest.mark.parametrize("bits,n", [(24, 0), (53, 0)])
+def test_fitter_reproduces_table1_from_scratch(bits, n):
+    # the fitter itself, not only its stored output: a fresh constrained
+    # minimax fit (Lawson, then Remez) at Table I's order N reaches Table I's
+    # exact-arithmetic accuracy eps_n, and v keeps no zero on [0, inf)
+    from paper_2504_07637_gb300.fit import boys_fit
+
+    t1 = _table1()[n]
+    N = t1[f"N{bits}"]
+    r = boys_fit.fit(n, N, bits)
+    got = float(-mp.log(r["E"], 2))
+    assert abs(got - t1[f"eps{bits}"]) <= 0.3, (got, t1[f"eps{bits}"])
+    # its Q~(0) = q0 puts Eq. "fq" at x = 0 on F_n(0) = 1/(2n+1): c_n q0^{-s^2} (2n+1) = 1
+    k = r["k"]
+    s2 = (mp.mpf(n) + mp.mpf(1) / 2) ** 2
+    assert abs(mp.mpf(k["c"]) * mp.mpf(k["q0"]) ** (-s2) * (2 * n + 1) - 1) < mp.mpf(10) ** -30
