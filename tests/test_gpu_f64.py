@@ -317,3 +317,25 @@ def test_small_and_large_launch_shapes_agree_bitwise(lib, n_max):
     big = lib.boys(x, n_max)
     parts = [lib.boys(x[i:i + (1 << 19)], n_max) for i in range(0, x.numel(), 1 << 19)]
     assert torch.equal(big, torch.cat(parts))
+
+
+def test_f0_equals_the_erf_closed_form(lib):
+    # an independent pin of the GPU path (no oracle): F_0(x) = sqrt(pi/x) erf(sqrt(x)) / 2,
+    # evaluated in mpmath at 30 digits, across the closed form and the asymptote
+    import torch
+
+    rng = np.random.default_rng(11)
+    x = np.exp(rng.uniform(math.log(1e-12), math.log(1e5), 2000))
+    got = lib.boys(torch.from_numpy(x).cuda(), 0).cpu().numpy()[:, 0]
+    try:
+        import mpmath as mp
+
+        mp.mp.dps = 30
+        want = np.array([float(mp.sqrt(mp.pi / xi) * mp.erf(mp.sqrt(xi)) / 2) for xi in map(mp.mpf, x)])
+        tol = 2e-15
+    except ImportError:  # scipy's double erf: a few ulp of its own
+        from scipy.special import erf
+
+        want = np.sqrt(np.pi / x) * erf(np.sqrt(x)) / 2
+        tol = 3e-15
+    assert np.max(np.abs(got / want - 1)) <= tol
