@@ -71,11 +71,22 @@ __device__ __forceinline__ void f32_emit(float *__restrict__ rows, int j, int64_
   }
 }
 
-// The contraction (MODE 1) is bound by instruction issue: compiled for 8
-// resident blocks of 128 threads (64 registers), it keeps enough warps to
-// fill the schedulers (measured faster than 72 registers and 7 blocks).
+// Minimum resident blocks each kernel is compiled for (launch bounds), as
+// measured on GB300 with 2^26 arguments:
+//  * the contraction (MODE 1) is bound by instruction issue: 8 blocks of 128
+//    threads (64 registers) keep enough warps to fill the schedulers (faster
+//    than 72 registers and 7 blocks);
+//  * rows up to n_max = 8: a minimum of 1 (the compiler then takes about 100
+//    registers; shared memory allows 5 blocks either way): 407 us against
+//    418 us with its default allocation (50 registers);
+//  * rows above n_max = 8: no minimum (52 registers): 721 us against 772 us.
+template <int NMAX, int MODE>
+constexpr int f32_min_blocks() {
+  return MODE == 1 ? 8 : (NMAX + 1 <= 9 ? 1 : 0);
+}
+
 template <int NMAX, int MODE, int BLOCK_ = 0, int TILE_ = 0>
-__global__ void __launch_bounds__(F32Tile<NMAX, MODE, BLOCK_, TILE_>::BLOCK, (MODE == 1 ? 8 : 1))
+__global__ void __launch_bounds__(F32Tile<NMAX, MODE, BLOCK_, TILE_>::BLOCK, (f32_min_blocks<NMAX, MODE>()))
     f32_split_kernel(const float *__restrict__ x, int64_t count, float *__restrict__ out, const F32Coef cf) {
   using P = F32Tile<NMAX, MODE, BLOCK_, TILE_>;
   static_assert(P::BLOCK >= 64 && P::TILE % P::BLOCK == 0 && P::TILE <= 65536, "shape");  // 64: the table load
