@@ -72,17 +72,18 @@ __device__ __forceinline__ void f32_emit(float *__restrict__ rows, int j, int64_
 }
 
 // Minimum resident blocks each kernel is compiled for (launch bounds), as
-// measured on GB300 with 2^26 arguments:
+// measured on GB300 (each setting in its own process):
 //  * the contraction (MODE 1) is bound by instruction issue: 8 blocks of 128
 //    threads (64 registers) keep enough warps to fill the schedulers (faster
-//    than 72 registers and 7 blocks);
-//  * rows up to n_max = 8: a minimum of 1 (the compiler then takes about 100
-//    registers; shared memory allows 5 blocks either way): 407 us against
-//    418 us with its default allocation (50 registers);
-//  * rows above n_max = 8: no minimum (52 registers): 721 us against 772 us.
+//    than 72 registers and 7 blocks, and than 116 registers and 4 blocks);
+//  * rows: a minimum of 1 lets the compiler take about 100 registers (shared
+//    memory bounds the resident blocks either way).  Over every order at 2^25
+//    arguments that is faster at n_max = 8, 9 and 15 (207 vs 215, 252 vs 258,
+//    415 vs 428 us) and slower elsewhere (2-8% at n_max = 0..7, 9% at 16), so
+//    only those orders ask for it.
 template <int NMAX, int MODE>
 constexpr int f32_min_blocks() {
-  return MODE == 1 ? 8 : (NMAX + 1 <= 9 ? 1 : 0);
+  return MODE == 1 ? 8 : ((NMAX == 8 || NMAX == 9 || NMAX == 15) ? 1 : 0);
 }
 
 template <int NMAX, int MODE, int BLOCK_ = 0, int TILE_ = 0>
