@@ -617,13 +617,18 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
         n_top = lib.boys_top_order_f64(n_max)
         z = lib.boys_cutoff(n_top, 53)
         fb = float(np.mean(x_host <= z))
-        if wl.get("two_point"):  # Trick B: n_bar = n_max / 2, closed forms at n_top and n_top(n_bar)
-            n_bar = n_max // 2
-            below, above = roofline.f64_counts_two_point(n_max, n_top, n_bar, lib.boys_top_order_f64(n_bar))
-        else:
-            below, above = roofline.f64_counts(n_max, n_top)
-        t_arg = sum((fb * below[k] + (1 - fb) * above[k]) / rates[k] for k in ("fma", "div", "sqrt", "exp", "rsqrt"))
+        def t_per_arg(int_chain):
+            if wl.get("two_point"):  # Trick B: n_bar = n_max / 2, closed forms at n_top and n_top(n_bar)
+                n_bar = n_max // 2
+                below, above = roofline.f64_counts_two_point(n_max, n_top, n_bar, lib.boys_top_order_f64(n_bar),
+                                                             int_chain)
+            else:
+                below, above = roofline.f64_counts(n_max, n_top, int_chain)
+            return sum((fb * below[k] + (1 - fb) * above[k]) / rates[k] for k in ("fma", "div", "sqrt", "exp", "rsqrt"))
+
+        t_arg = t_per_arg(True)
         achieved = t_arg * rates["fma"] * count / (ms / 1e3) / 1e12
+        achieved64 = t_per_arg(False) * rates["fma"] * count / (ms / 1e3) / 1e12
         peak = rates["fma"] / 1e12
         res["roofline"] = {
             "bound": "alu",
@@ -633,8 +638,12 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
             "frac": round(achieved / peak, 4),
             "traffic": None if wl.get("two_point") else traffic_record(f"f64_split_kernel<{n_max}>/scale_2^26"),
             "note": "FP64-pipe instruction equivalents per second (1 per add/mul/fma; exp, sqrt, rsqrt and div "
-            "weighted by their measured cost) vs the DFMA rate measured in this run; "
-            f"{fb:.3f} of arguments below z_{{{n_top},53}}",
+            "weighted by their measured cost) vs the DFMA rate measured in this run; the asymptote's upward "
+            f"product chain ({roofline.int_chain_orders(n_max)} orders) runs on the integer pipes and is not "
+            f"counted; {fb:.3f} of arguments below z_{{{n_top},53}}",
+            "all_fp64": {"achieved": round(achieved64, 5), "frac": round(achieved64 / peak, 4),
+                         "note": "the same evaluation with the asymptote's chain as two FP64 multiplications per "
+                         "order: the bound of an all-FP64 kernel (above 1: faster than that bound)"},
             "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 4),
                     "peak_source": hbm_src},
             "nominal": {"peak": F64_NOMINAL_TFMA, "frac": round(achieved / F64_NOMINAL_TFMA, 4),
@@ -880,6 +889,8 @@ def main():
             if "roofline" in r:
                 suite[name]["roofline_bound"] = r["roofline"]["bound"]
                 suite[name]["roofline_frac"] = r["roofline"]["frac"]
+                if "all_fp64" in r["roofline"]:
+                    suite[name]["all_fp64_frac"] = r["roofline"]["all_fp64"]["frac"]
         # the float path against the double one on the same arguments and order (n_max = 8)
         suite["scale_f32_n8"]["speedup_vs_f64_n8"] = round(suite["scale_f32_n8"]["value"] / value, 2)
         for name in ("contract_f64_n8", "contract_f32_n8"):

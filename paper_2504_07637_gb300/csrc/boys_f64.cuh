@@ -24,6 +24,7 @@
 
 #include "boys_coeffs_f64.inc"
 #include "boys_common.cuh"
+#include "boys_sig64.cuh"
 
 #include <climits>
 #include <type_traits>
@@ -138,7 +139,7 @@ __device__ __forceinline__ void f64_formula_two(const double x, double (&F)[NMAX
 // F_0 = c_0 / sqrt(x), F_m = F_{m-1} (m - 1/2) / x so that high orders
 // underflow gracefully.  Negative x and NaN give NaN through rsqrt.
 template <int NMAX>
-__device__ __forceinline__ void f64_asymptote(const double x, double (&F)[NMAX + 1]) {
+__device__ __forceinline__ void f64_asymptote_fp64(const double x, double (&F)[NMAX + 1]) {
   const double rs = rsqrt(x);
   double f = 0.88622692545275801365 * rs;  // c_0 = sqrt(pi)/2
   F[0] = f;
@@ -158,6 +159,66 @@ __device__ __forceinline__ void static_for(Fn &&f) {
   if constexpr ((STEP > 0 && I < END) || (STEP < 0 && I > END)) {
     f(std::integral_constant<int, I>{});
     static_for<I + STEP, END, STEP>(f);
+  }
+}
+
+// x > 0 below the bound of the integer chain for rows up to NMAX (this
+// excludes negative x, NaN and +inf).
+template <int NMAX>
+__device__ __forceinline__ bool sig64_chain_ok(const double x) {
+  return (unsigned long long)__double_as_longlong(x) < sig64_chain_xmax_bits(NMAX);
+}
+
+// The asymptote of f64_asymptote_fp64 with its product chain on the integer
+// pipes (boys_sig64.cuh): F_0 = c_0 rsqrt(x) and y = 1/x in FP64, then
+// z_m = F_0 y^m and F_m = z_m prod_{k<=m} (k - 1/2) as 64-bit significands,
+// each F_m rounded once.  Requires sig64_chain_ok<NMAX>(x).
+struct Sig64Chain {
+  unsigned long long s, sy;
+  int e, ey;
+  __device__ __forceinline__ void start(const double f0, const double y) {
+    const unsigned long long fb = __double_as_longlong(f0), yb = __double_as_longlong(y);
+    s = sig64_of_bits(fb);
+    e = exp_of_bits(fb);
+    sy = sig64_of_bits(yb);
+    ey = exp_of_bits(yb);
+  }
+  // z_m from z_{m-1}, and F_m
+  template <int M>
+  __device__ __forceinline__ double next() {
+    constexpr Sig64 h = half_odd_product(M);
+    uint64_t zs = s;
+    sig64_mul(zs, e, sy, ey);
+    s = zs;
+    uint64_t w = zs;
+    int ew = e;
+    sig64_mul(w, ew, h.s, h.e);
+    return __longlong_as_double((long long)sig64_round_bits(w, ew));
+  }
+};
+
+template <int NMAX>
+__device__ __forceinline__ void f64_asymptote_int(const double x, double (&F)[NMAX + 1]) {
+  const double rs = rsqrt(x);
+  F[0] = 0.88622692545275801365 * rs;
+  if constexpr (NMAX >= 1) {
+    Sig64Chain ch;
+    ch.start(F[0], NMAX <= 12 ? rs * rs : 1.0 / x);
+    static_for<1, NMAX + 1, 1>([&](auto mc) {
+      constexpr int m = decltype(mc)::value;
+      F[m] = ch.template next<m>();
+    });
+  }
+}
+
+// The asymptote row: on the integer pipes where the chain's range allows
+// (every argument of the benchmark distributions), else in FP64.
+template <int NMAX>
+__device__ __forceinline__ void f64_asymptote(const double x, double (&F)[NMAX + 1]) {
+  if (NMAX >= 1 && sig64_chain_ok<NMAX>(x)) {
+    f64_asymptote_int<NMAX>(x, F);
+  } else {
+    f64_asymptote_fp64<NMAX>(x, F);
   }
 }
 
@@ -248,18 +309,36 @@ __device__ __forceinline__ void f64_formula_staged(const double (&x)[K], const i
   }
 }
 
-// f64_asymptote for the K entries of every lane of a full warp, staged.
+// f64_asymptote for the K entries of every lane of a full warp, staged; the
+// chain runs on the integer pipes when every entry of the warp allows it.
 template <int NMAX, int CH, int K>
 __device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const int (&j)[K],
                                                      double *__restrict__ out, double *__restrict__ stg,
                                                      const int lane) {
   constexpr int W = NMAX + 1;
   double f[K], y[K];
+  bool ok = true;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const double rs = rsqrt(x[k]);
     f[k] = 0.88622692545275801365 * rs;
     y[k] = NMAX <= 12 ? rs * rs : 1.0 / x[k];
+    ok = ok && sig64_chain_ok<NMAX>(x[k]);
+  }
+  if (__all_sync(0xffffffffu, ok)) {
+    Sig64Chain ch[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) ch[k].start(f[k], y[k]);
+    static_for<0, W, 1>([&](auto mc) {
+      constexpr int m = decltype(mc)::value;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if constexpr (m > 0) f[k] = ch[k].template next<m>();
+        stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + m % CH] = f[k];
+      }
+      if constexpr (m % CH == CH - 1 || m == NMAX) f64_stage_flush<W, CH, K, m % CH + 1>(out, stg, m - m % CH, j, lane);
+    });
+    return;
   }
   static_for<0, W, 1>([&](auto mc) {
     constexpr int m = decltype(mc)::value;

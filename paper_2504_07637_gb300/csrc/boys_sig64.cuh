@@ -1,0 +1,104 @@
+// 64-bit significand arithmetic on the integer pipes.
+//
+// Above the cut-off the Boys row is the asymptote of Eq. "limf1",
+// F_m = F_0 prod_{k<=m} (k - 1/2) / x, a chain of 2 n_max double
+// multiplications.  GB300 retires about 1.7 FP64 operations per clock per SM,
+// but its integer pipes take 32-bit multiply-adds at a far higher rate, and
+// in this kernel they are nearly idle.  So the chain runs on integers:
+// values are s 2^(e - 63) with a 64-bit significand s in [2^63, 2^64), one
+// product is three 32 x 32 -> 64-bit multiply-adds, and each F_m is rounded
+// to a double once.  With 11 guard bits every F_m is within one rounding of
+// the exact chain from F_0 and 1/x, against 2m roundings for the double
+// chain.
+//
+// Everything here is plain integer arithmetic, valid on the host too.
+#pragma once
+
+#include <cstdint>
+
+#if defined(__CUDACC__)
+#define BOYS_HD __host__ __device__ __forceinline__
+#define BOYS_HD_CONSTEXPR __host__ __device__ constexpr
+#else
+#define BOYS_HD inline
+#define BOYS_HD_CONSTEXPR constexpr
+#endif
+
+namespace boys {
+
+// A positive number s 2^(e - 63), s in [2^63, 2^64).
+struct Sig64 {
+  uint64_t s;
+  int e;
+};
+
+// floor(a b / 2^64) minus at most 1: with a = a1 2^32 + a0 and b likewise,
+// a b = a1 b1 2^64 + (a1 b0 + a0 b1) 2^32 + a0 b0, and the low half of the
+// cross products' sum and all of a0 b0 (together below 2^65) are left out.
+// For a, b >= 2^63 the result is at least 2^62, so its relative error is
+// below 2^-62.
+BOYS_HD uint64_t mulhi_trunc(uint64_t a, uint64_t b) {
+  const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+  const uint64_t u = (uint64_t)a0 * b1;
+  // a1 b0 + (u mod 2^32) <= (2^32 - 1)^2 + 2^32 - 1 < 2^64: no overflow
+  const uint64_t v = (uint64_t)a1 * b0 + (uint32_t)u;
+  return (uint64_t)a1 * b1 + (u >> 32) + (v >> 32);
+}
+
+// The significand and exponent of a positive normal double, from its bits.
+BOYS_HD uint64_t sig64_of_bits(uint64_t bits) { return (bits << 11) | (1ull << 63); }
+BOYS_HD int exp_of_bits(uint64_t bits) { return (int)(bits >> 52) - 1023; }
+
+// The product of two Sig64 numbers: (s_a, e_a) (s_b, e_b) -> (s, e).
+// mulhi_trunc gives t in [2^62, 2^64), the product being t 2^(e_a + e_b - 62);
+// one left shift when t < 2^63 normalises it.
+BOYS_HD void sig64_mul(uint64_t &s, int &e, uint64_t sb, int eb) {
+  const uint64_t t = mulhi_trunc(s, sb);
+  const int top = (int)(t >> 63);
+  s = top ? t : t << 1;
+  e += eb + top;
+}
+
+// The bits of the double nearest s 2^(e - 63) (ties away from zero), for a
+// result in the normal range (-1022 <= e <= 1023).  Rounding up to 2^53
+// carries into the exponent field, which is the right value.
+BOYS_HD uint64_t sig64_round_bits(uint64_t s, int e) {
+  const uint64_t m = (s >> 11) + ((s >> 10) & 1);
+  return m + ((uint64_t)(e + 1022) << 52);
+}
+
+// prod_{k=1}^{m} (k - 1/2) = (2m - 1)!! / 2^m as a Sig64, each factor
+// applied exactly and the product rounded to 64 bits (relative error below
+// m 2^-64).  (2k - 1) s needs at most 71 bits, held as hi 2^32 + lo.
+BOYS_HD_CONSTEXPR Sig64 half_odd_product(int m) {
+  uint64_t s = 1ull << 63;
+  int e = 0;
+  for (int k = 1; k <= m; ++k) {
+    const uint64_t odd = (uint64_t)(2 * k - 1);
+    const uint64_t plo = (s & 0xffffffffull) * odd;
+    const uint64_t hi = (s >> 32) * odd + (plo >> 32);
+    const uint64_t lo = plo & 0xffffffffull;
+    int r = 0;  // the product is in [2^(63 + r), 2^(64 + r))
+    while ((hi >> (32 + r)) != 0) ++r;
+    uint64_t t = (hi << (32 - r)) | (lo >> r);
+    if (r > 0) t += (lo >> (r - 1)) & 1;  // round to nearest
+    if (t == 0) {                         // rounded up to 2^64
+      t = 1ull << 63;
+      ++r;
+    }
+    s = t;
+    e += r - 1;  // (k - 1/2) = (2k - 1) / 2
+  }
+  return Sig64{s, e};
+}
+
+// The bits of a bound x_max below which the integer chain gives every F_m,
+// m <= n_max, in the normal range: for x < 2^floor(2038/(2n+1)),
+// F_n(x) >= c_1 x^-(n+1/2) > 2^-1021 (n >= 1), and 1/x is normal.  +inf when
+// the bound is beyond the double range (n_max = 0, where there is no chain).
+BOYS_HD_CONSTEXPR uint64_t sig64_chain_xmax_bits(int n_max) {
+  const int l = 2038 / (2 * n_max + 1);
+  return l >= 1024 ? 0x7ff0000000000000ull : (uint64_t)(l + 1023) << 52;
+}
+
+}  // namespace boys

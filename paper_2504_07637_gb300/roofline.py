@@ -5,9 +5,10 @@ cut-off one evaluation of Q~ in root-product form, one division u/v, one
 exponential (shared with the recursion, Eq. "r"), the half-integer powers
 Q^{n+1/2} and D^{-(n+1/2)} as square-and-multiply plus a reciprocal square
 root each, and two operations per step of the downward recursion; above it
-(Eq. "limf1") one reciprocal square root and two operations per order.  "fma" counts every add, multiply or fused multiply-add
-(each one FP64-pipe instruction).  Bytes per argument are the input value plus
-the n_max+1 outputs.
+(Eq. "limf1") one reciprocal square root, F_0 and 1/x, the upward product
+chain running on the integer pipes.  "fma" counts every add, multiply or
+fused multiply-add (each one FP64-pipe instruction).  Bytes per argument are
+the input value plus the n_max+1 outputs.
 """
 from __future__ import annotations
 
@@ -56,12 +57,16 @@ def _closed_form_counts(n_top: int) -> dict:
     return {"fma": fma, "div": div, "sqrt": 0, "exp": 0, "rsqrt": rsq}
 
 
-def _asymptote_counts(n_max: int) -> dict:
-    """Operations of the asymptote row (Eq. "limf1"): one reciprocal square
-    root, 1/x as rsqrt(x)^2 for n_max <= 12 (else a division), and two
-    operations per order."""
+def _asymptote_counts(n_max: int, int_chain: bool = True) -> dict:
+    """FP64 operations of the asymptote row (Eq. "limf1"): one reciprocal
+    square root, F_0 = c_0 rsqrt(x), 1/x as rsqrt(x)^2 for n_max <= 12 (else
+    a division), and the upward chain F_m = F_{m-1} (m - 1/2) / x.  The
+    kernels run that chain on 64-bit integer significands (csrc/boys_sig64.cuh),
+    which leaves the FP64 pipe with F_0 and 1/x only; int_chain=False counts
+    it as two FP64 multiplications per order instead."""
+    y = 0 if n_max == 0 else (1 if n_max <= 12 else 0)
     return {
-        "fma": 1 + (1 if n_max <= 12 else 0) + 2 * n_max,
+        "fma": 1 + y + (0 if int_chain else 2 * n_max),
         "div": 0 if n_max <= 12 else 1,
         "sqrt": 0,
         "exp": 0,
@@ -69,18 +74,26 @@ def _asymptote_counts(n_max: int) -> dict:
     }
 
 
-def f64_counts(n_max: int, n_top: int) -> tuple[dict, dict]:
-    """(below-cut-off, above-cut-off) operation counts per argument, in the
-    form the double kernels evaluate them: the closed form at n_top, one
+def int_chain_orders(n_max: int) -> int:
+    """Orders of the asymptote row computed on the integer pipes (two 64-bit
+    significand products and one rounding each)."""
+    return n_max
+
+
+def f64_counts(n_max: int, n_top: int, int_chain: bool = True) -> tuple[dict, dict]:
+    """(below-cut-off, above-cut-off) FP64 operation counts per argument, in
+    the form the double kernels evaluate them: the closed form at n_top, one
     exponential and two operations per step of the downward recursion (Eq.
-    "r") below the cut-off; the asymptote above it."""
+    "r") below the cut-off; the asymptote above it (its chain on the integer
+    pipes unless int_chain is False)."""
     below = _closed_form_counts(n_top)
     below["exp"] = 1
     below["fma"] += 2 * n_top  # recursion
-    return below, _asymptote_counts(n_max)
+    return below, _asymptote_counts(n_max, int_chain)
 
 
-def f64_counts_two_point(n_max: int, n_top: int, n_bar: int, n_top_lo: int) -> tuple[dict, dict]:
+def f64_counts_two_point(n_max: int, n_top: int, n_bar: int, n_top_lo: int,
+                         int_chain: bool = True) -> tuple[dict, dict]:
     """As f64_counts for the two-point evaluation (Trick B of Sec. 3): closed
     forms at n_top and at n_top_lo sharing one exponential, the recursion
     from n_top down to n_bar + 1 and the one from n_top_lo down to 0."""
@@ -90,17 +103,17 @@ def f64_counts_two_point(n_max: int, n_top: int, n_bar: int, n_top_lo: int) -> t
         below[k] += lo[k]
     below["exp"] = 1
     below["fma"] += 2 * (n_top - (n_bar + 1)) + 2 * n_top_lo
-    return below, _asymptote_counts(n_max)
+    return below, _asymptote_counts(n_max, int_chain)
 
 
-def f64_counts_contract(n_max: int, n_top: int, uniform: bool = True) -> tuple[dict, dict]:
+def f64_counts_contract(n_max: int, n_top: int, uniform: bool = True, int_chain: bool = True) -> tuple[dict, dict]:
     """As f64_counts for the fused contraction sum_m c_m F_m: below the
     cut-off the row as f64_counts plus the n_max + 1 term dot product; above
     it, with the same coefficients for every argument and n_max <= 16, the
     contraction of the asymptote as a polynomial in y = 1/x (Horner, n_max
     fused multiply-adds, y and two products), else the asymptote row and the
     dot product."""
-    below, above = f64_counts(n_max, n_top)
+    below, above = f64_counts(n_max, n_top, int_chain)
     below["fma"] += n_max + 1
     if uniform and n_max <= 16:
         # y = rs^2 (n_max <= 12) or 1/x, needed only from n_max = 1 on

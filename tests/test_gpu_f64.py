@@ -119,6 +119,30 @@ def test_special_arguments(lib, oracle_mod):
     assert np.max(np.abs(zero * (2 * np.arange(37) + 1) - 1)) <= TOL
 
 
+@pytest.mark.parametrize("n_max", [1, 8, 11, 12, 13, 16, 36])
+def test_asymptote_on_both_sides_of_the_integer_chain_bound(lib, oracle_mod, n_max, record_property):
+    """Above the cut-off the row's product chain runs on 64-bit integer
+    significands for x < 2^floor(2038/(2 n_max + 1)) (where every F_m is a
+    normal double) and in FP64 from there on.  Arguments on both sides of
+    that bound, up to where the rows underflow, share warps and must match
+    the oracle; so must the row's own ragged tail of one argument."""
+    xmax = math.ldexp(1.0, min(2038 // (2 * n_max + 1), 1023))
+    rng = np.random.default_rng(2504 + n_max)
+    lo = math.log(lib.cutoff(n_max + 4, 53))
+    hi = math.log(min(xmax * 1e6, 1.7e308))
+    x = np.exp(rng.uniform(lo, hi, 8191))
+    edge = [np.nextafter(xmax, 0), xmax, np.nextafter(xmax, np.inf), 2 * xmax]
+    x = np.concatenate([x, [v for v in edge if np.isfinite(v)]])
+    rng.shuffle(x)
+    got = _gpu(lib, x, n_max)
+    ref = oracle_mod.boys(x, n_max)
+    rel = _relerr(got, ref)
+    record_property("max_rel_err_per_m", _per_m(rel))
+    below = x < xmax
+    assert below.sum() > 1000 and (~below).sum() > (0 if n_max == 1 else 1000)
+    assert rel.max() <= TOL, (n_max, x[np.argmax(rel.max(axis=1))])
+
+
 @pytest.mark.parametrize("two_point", [False, True])
 @pytest.mark.parametrize("n_max", [8, 16, 36])
 def test_domain_convention_every_layout(lib, n_max, two_point):

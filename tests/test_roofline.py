@@ -73,6 +73,21 @@ def test_contraction_counts():
         b, a = roofline.f64_counts_contract(n_max, n_top, uniform=True)
         assert b["fma"] == row_b["fma"] + n_max + 1 and b["exp"] == 1
         assert a["fma"] == n_max + 2 + (1 if 1 <= n_max <= 12 else 0) and a["rsqrt"] == 1
-        assert a["fma"] < row_a["fma"] + n_max + 1  # cheaper than the row and its dot product
+        # cheaper than the row and its dot product in FP64; with the row's chain
+        # on the integer pipes, no dearer than the row and its dot product
+        fp64_row = roofline.f64_counts(n_max, n_top, int_chain=False)[1]["fma"]
+        assert a["fma"] < fp64_row + n_max + 1 or n_max == 0
+        assert a["fma"] <= row_a["fma"] + n_max + 1
     b, a = roofline.f64_counts_contract(36, 40, uniform=True)  # no Horner above n_max = 16
     assert a["fma"] == roofline.f64_counts(36, 40)[1]["fma"] + 37
+
+
+def test_asymptote_chain_leaves_the_fp64_pipe():
+    # the upward chain's two multiplications per order run on the integer
+    # pipes; F_0 = c_0 rsqrt(x) and y = 1/x stay in FP64
+    for n_max in (0, 1, 8, 12, 13, 36):
+        _, a = roofline.f64_counts(n_max, n_max)
+        _, a64 = roofline.f64_counts(n_max, n_max, int_chain=False)
+        assert a64["fma"] - a["fma"] == 2 * n_max == 2 * roofline.int_chain_orders(n_max)
+        assert a["fma"] == 1 + (1 if 1 <= n_max <= 12 else 0) and a["rsqrt"] == 1
+        assert a["div"] == a64["div"] == (1 if n_max > 12 else 0)
