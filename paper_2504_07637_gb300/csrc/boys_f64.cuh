@@ -39,6 +39,15 @@ constexpr int kNoRow = INT_MIN;
 
 static_assert(f64_top_order(kMaxNF64) <= BOYS_F64_TABLE_MAX_N, "fitted table too short");
 
+// Compile-time loop: f(std::integral_constant<int, i>) for i = I, I + STEP, ... while i has not reached END.
+template <int I, int END, int STEP, typename Fn>
+__device__ __forceinline__ void static_for(Fn &&f) {
+  if constexpr ((STEP > 0 && I < END) || (STEP < 0 && I > END)) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + STEP, END, STEP>(f);
+  }
+}
+
 __device__ __forceinline__ double twice(double x) {
   // exact 2x for normal x; for |x| below the normal range the result is a
   // tiny normal number, which leaves fma(2x, F, e^{-x}) unchanged
@@ -96,16 +105,98 @@ __device__ __forceinline__ double f64_closed_form(const double x, const double e
   }
 }
 
-// Downward recursion of Eq. "r" from F_TOP to F_LO, storing F_m for
-// LO <= m <= min(TOP, NMAX).
-template <int TOP, int LO, int NMAX>
-__device__ __forceinline__ void f64_recurse(double f, const double tx, const double e, double (&F)[NMAX + 1]) {
-#pragma unroll
-  for (int m = TOP; m > LO; --m) {
-    if (m <= NMAX) F[m] = f;
-    f = fma(tx, f, e) * (1.0 / double(2 * m - 1));
+// Constants of the integer loops that run over orders at run time, indexed
+// by the order m: 1/(2m - 1) for the recursion (m >= 1) and
+// prod_{k<=m} (k - 1/2) for the asymptote's chain.
+constexpr int kSig64TabLen = BOYS_F64_TABLE_MAX_N + 1;
+struct Sig64Tab {
+  uint64_t s[kSig64TabLen];
+  int e[kSig64TabLen];
+};
+__host__ __device__ constexpr Sig64Tab make_sig64_tab(bool recip) {
+  Sig64Tab t{};
+  for (int m = 0; m < kSig64TabLen; ++m) {
+    const Sig64 v = recip ? recip_odd(m == 0 ? 1 : 2 * m - 1) : half_odd_product(m);
+    t.s[m] = v.s;
+    t.e[m] = v.e;
   }
-  if (LO <= NMAX) F[LO] = f;
+  return t;
+}
+static __constant__ Sig64Tab kRecipOddTab = make_sig64_tab(true);
+static __constant__ Sig64Tab kHalfOddTab = make_sig64_tab(false);
+
+// The downward recursion's state on the integer pipes (boys_sig64.cuh):
+// F_m, 2x and e^{-x} as 64-bit significands.  One step,
+// F_{m-1} = (2x F_m + e^{-x}) (1/(2m - 1)), is a product, an aligned sum of
+// two positive numbers and a product with a constant; F_m is rounded to a
+// double only where it is stored.  For x = 0 (twice(x) is then 2^-1022) the
+// product is shifted out of the sum, as in FP64.
+struct Sig64Down {
+  uint64_t sf, sx, se;
+  int ef, ex, ee;
+  __device__ __forceinline__ void start(const double f, const double tx, const double e) {
+    const uint64_t fb = __double_as_longlong(f), xb = __double_as_longlong(tx), eb = __double_as_longlong(e);
+    sf = sig64_of_bits(fb);
+    ef = exp_of_bits(fb);
+    sx = sig64_of_bits(xb);
+    ex = exp_of_bits(xb);
+    se = sig64_of_bits(eb);
+    ee = exp_of_bits(eb);
+  }
+  // F_{M-1} from F_M
+  template <int M>
+  __device__ __forceinline__ void step() {
+    constexpr Sig64 k = recip_odd(2 * M - 1);
+    sig64_mul(sf, ef, sx, ex);
+    sig64_add(sf, ef, se, ee);
+    if constexpr (M > 1) sig64_mul(sf, ef, k.s, k.e);
+  }
+  // the same for an order m >= 1 known at run time (for m = 1 the factor 1
+  // clears the significand's last bit, a relative change below 2^-63)
+  __device__ __forceinline__ void step_rt(const int m) {
+    const uint64_t ks = kRecipOddTab.s[m];
+    const int ke = kRecipOddTab.e[m];
+    sig64_mul(sf, ef, sx, ex);
+    sig64_add(sf, ef, se, ee);
+    sig64_mul(sf, ef, ks, ke);
+  }
+  __device__ __forceinline__ double value() const { return __longlong_as_double((long long)sig64_round_bits(sf, ef)); }
+};
+
+// Whether an unstaged kernel (rows below n_max = 12, the fused contraction,
+// the gradient) runs its recursion on the integer pipes, by the number of
+// steps it unrolls per list entry.  An integer step is about 36 instructions
+// against the FP64 step's 2: unrolled over all 41 steps at n_max = 36, with
+// two entries per lane, the row kernels fell from 190 to 139 G values/s,
+// presumably as their code (about 80 KB) outgrew the instruction cache.  The
+// staged one-point row kernels (n_max >= 12) loop over chunks of orders
+// instead (f64_recurse_staged) and always take the integer pipes: n_max = 36
+// then ran at 202 G values/s (190 with the FP64 recursion).
+__host__ __device__ constexpr bool f64_int_recursion(int steps) { return steps <= 18; }
+
+// Eq. "r" from F_TOP (in f) down to F_LO, storing F_m for m <= NMAX: on the
+// integer pipes (INT), else in FP64.
+template <int TOP, int LO, int NMAX, bool INT = f64_int_recursion(TOP - LO)>
+__device__ __forceinline__ void f64_recurse(double f, const double tx, const double e, double (&F)[NMAX + 1]) {
+  if constexpr (!INT) {
+#pragma unroll
+    for (int m = TOP; m > LO; --m) {
+      if (m <= NMAX) F[m] = f;
+      f = fma(tx, f, e) * (1.0 / double(2 * m - 1));
+    }
+    if (LO <= NMAX) F[LO] = f;
+  } else {
+    if constexpr (TOP <= NMAX) F[TOP] = f;
+    if constexpr (TOP > LO) {
+      Sig64Down r;
+      r.start(f, tx, e);
+      static_for<TOP, LO, -1>([&](auto mc) {
+        constexpr int m = decltype(mc)::value;
+        r.template step<m>();
+        if constexpr (m - 1 <= NMAX) F[m - 1] = r.value();
+      });
+    }
+  }
 }
 
 template <int NTOP, int NMAX>
@@ -125,11 +216,12 @@ template <int NTOP, int NTOP_LO, int NBAR, int NMAX>
 __device__ __forceinline__ void f64_formula_two(const double x, double (&F)[NMAX + 1],
                                                 const double *__restrict__ tab64) {
   static_assert(NBAR < NMAX && NTOP_LO >= NBAR && NTOP_LO < NTOP, "orders");
+  constexpr bool INT = f64_int_recursion(NTOP - NBAR - 1 + NTOP_LO);
   const double e = exp_neg(x, tab64);
   const double tx = twice(x);
-  f64_recurse<NTOP, NBAR + 1, NMAX>(f64_closed_form<NTOP>(x, e), tx, e, F);
+  f64_recurse<NTOP, NBAR + 1, NMAX, INT>(f64_closed_form<NTOP>(x, e), tx, e, F);
   double lo[NBAR + 1];
-  f64_recurse<NTOP_LO, 0, NBAR>(f64_closed_form<NTOP_LO>(x, e), tx, e, lo);
+  f64_recurse<NTOP_LO, 0, NBAR, INT>(f64_closed_form<NTOP_LO>(x, e), tx, e, lo);
 #pragma unroll
   for (int m = 0; m <= NBAR; ++m) F[m] = lo[m];
 }
@@ -153,15 +245,6 @@ __device__ __forceinline__ void f64_asymptote_fp64(const double x, double (&F)[N
   }
 }
 
-// Compile-time loop: f(std::integral_constant<int, i>) for i = I, I + STEP, ... while i has not reached END.
-template <int I, int END, int STEP, typename Fn>
-__device__ __forceinline__ void static_for(Fn &&f) {
-  if constexpr ((STEP > 0 && I < END) || (STEP < 0 && I > END)) {
-    f(std::integral_constant<int, I>{});
-    static_for<I + STEP, END, STEP>(f);
-  }
-}
-
 // x > 0 below the bound of the integer chain for rows up to NMAX (this
 // excludes negative x, NaN and +inf).
 template <int NMAX>
@@ -174,10 +257,10 @@ __device__ __forceinline__ bool sig64_chain_ok(const double x) {
 // z_m = F_0 y^m and F_m = z_m prod_{k<=m} (k - 1/2) as 64-bit significands,
 // each F_m rounded once.  Requires sig64_chain_ok<NMAX>(x).
 struct Sig64Chain {
-  unsigned long long s, sy;
+  uint64_t s, sy;
   int e, ey;
   __device__ __forceinline__ void start(const double f0, const double y) {
-    const unsigned long long fb = __double_as_longlong(f0), yb = __double_as_longlong(y);
+    const uint64_t fb = __double_as_longlong(f0), yb = __double_as_longlong(y);
     s = sig64_of_bits(fb);
     e = exp_of_bits(fb);
     sy = sig64_of_bits(yb);
@@ -187,12 +270,18 @@ struct Sig64Chain {
   template <int M>
   __device__ __forceinline__ double next() {
     constexpr Sig64 h = half_odd_product(M);
-    uint64_t zs = s;
-    sig64_mul(zs, e, sy, ey);
-    s = zs;
-    uint64_t w = zs;
+    sig64_mul(s, e, sy, ey);
+    uint64_t w = s;
     int ew = e;
     sig64_mul(w, ew, h.s, h.e);
+    return __longlong_as_double((long long)sig64_round_bits(w, ew));
+  }
+  // the same for an order m >= 1 known at run time
+  __device__ __forceinline__ double next_rt(const int m) {
+    sig64_mul(s, e, sy, ey);
+    uint64_t w = s;
+    int ew = e;
+    sig64_mul(w, ew, kHalfOddTab.s[m], kHalfOddTab.e[m]);
     return __longlong_as_double((long long)sig64_round_bits(w, ew));
   }
 };
@@ -263,22 +352,71 @@ __device__ __forceinline__ void f64_stage_flush(double *__restrict__ out, const 
 // LO <= m <= HI and flushing every chunk of CH orders whose lowest order is
 // reached (orders above HI of that chunk were staged before, by the other
 // recursion of a two-point evaluation).  The arithmetic is f64_recurse's.
-template <int TOP, int LO, int HI, int W, int CH, int K>
-__device__ __forceinline__ void f64_recurse_staged(double (&f)[K], const double (&tx)[K], const double (&e)[K],
+template <int TOP, int LO, int HI, int W, int CH, int K, bool INT>
+__device__ __forceinline__ void f64_recurse_staged(const double (&f0)[K], const double (&tx)[K], const double (&e)[K],
                                                    const int (&j)[K], double *__restrict__ out,
                                                    double *__restrict__ stg, const int lane) {
-  static_for<TOP, LO - 1, -1>([&](auto mc) {
-    constexpr int m = decltype(mc)::value;
-    if constexpr (m <= HI) {
+  if constexpr (!INT) {
+    double f[K];
 #pragma unroll
-      for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + m % CH] = f[k];
-      if constexpr (m % CH == 0) f64_stage_flush<W, CH, K, (W - m < CH ? W - m : CH)>(out, stg, m, j, lane);
-    }
-    if constexpr (m > LO) {
+    for (int k = 0; k < K; ++k) f[k] = f0[k];
+    static_for<TOP, LO - 1, -1>([&](auto mc) {
+      constexpr int m = decltype(mc)::value;
+      if constexpr (m <= HI) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) f[k] = fma(tx[k], f[k], e[k]) * (1.0 / double(2 * m - 1));
+        for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + m % CH] = f[k];
+        if constexpr (m % CH == 0) f64_stage_flush<W, CH, K, (W - m < CH ? W - m : CH)>(out, stg, m, j, lane);
+      }
+      if constexpr (m > LO) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) f[k] = fma(tx[k], f[k], e[k]) * (1.0 / double(2 * m - 1));
+      }
+    });
+  } else {
+    // On the integer pipes.  Whole chunks of CH orders that are all staged,
+    // flushed in full and above LO - 1 run in a loop over the chunks (an
+    // integer step is ~36 instructions, and unrolled over every order the
+    // code of the high orders outgrew the instruction cache); the orders
+    // above them (from TOP) and below them (down to LO) are unrolled.
+    Sig64Down r[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) r[k].start(f0[k], tx[k], e[k]);
+    constexpr int TOPM = HI < TOP - 1 ? HI : TOP - 1;  // highest order a looped chunk may hold
+    constexpr int CT = (TOPM + 1) / CH - 1;            // highest such chunk
+    constexpr int CB = (LO + CH - 1) / CH;             // lowest chunk that starts at or above LO
+    constexpr int MT = CT >= CB ? CH * (CT + 1) : LO;  // orders TOP .. MT unrolled before the loop
+    auto unrolled = [&](auto mc) {
+      constexpr int m = decltype(mc)::value;
+      if constexpr (m <= HI) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + m % CH] = m == TOP ? f0[k] : r[k].value();
+        if constexpr (m % CH == 0) f64_stage_flush<W, CH, K, (W - m < CH ? W - m : CH)>(out, stg, m, j, lane);
+      }
+      if constexpr (m > LO) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) r[k].template step<m>();
+      }
+    };
+    static_for<TOP, MT - 1, -1>(unrolled);
+    if constexpr (CT >= CB) {
+#pragma unroll 1
+      for (int c = CT; c >= CB; --c) {
+        const int m0 = c * CH;
+#pragma unroll
+        for (int i = CH - 1; i >= 0; --i) {
+#pragma unroll
+          for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + i] = r[k].value();
+          if (i == 0) f64_stage_flush<W, CH, K, CH>(out, stg, m0, j, lane);
+          if (m0 + i > LO) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) r[k].step_rt(m0 + i);
+          }
+        }
+      }
+      static_for<CH * CB - 1, LO - 1, -1>(unrolled);
     }
-  });
+  }
 }
 
 // f64_formula (TWO = false) or f64_formula_two (TWO = true) for the K
@@ -297,15 +435,19 @@ __device__ __forceinline__ void f64_formula_staged(const double (&x)[K], const i
     f[k] = f64_closed_form<NTOP>(x[k], e[k]);
   }
   if constexpr (!TWO) {
-    f64_recurse_staged<NTOP, 0, NMAX, W, CH, K>(f, tx, e, j, out, stg, lane);
+    f64_recurse_staged<NTOP, 0, NMAX, W, CH, K, true>(f, tx, e, j, out, stg, lane);
   } else {
     constexpr int NBAR = f64_two_point_nbar(NMAX);
     constexpr int NTOP_LO = f64_top_order(NBAR);
     static_assert(NBAR < NMAX && NTOP_LO >= NBAR && NTOP_LO < NTOP, "orders");
-    f64_recurse_staged<NTOP, NBAR + 1, NMAX, W, CH, K>(f, tx, e, j, out, stg, lane);
+    // two closed forms per argument leave less room for integer work: at
+    // n_max = 36 the two-point rows measured 148 G values/s with both
+    // recursions in FP64 and 139 on the integer pipes
+    constexpr bool INT = f64_int_recursion(NTOP - NBAR - 1 + NTOP_LO);
+    f64_recurse_staged<NTOP, NBAR + 1, NMAX, W, CH, K, INT>(f, tx, e, j, out, stg, lane);
 #pragma unroll
     for (int k = 0; k < K; ++k) f[k] = f64_closed_form<NTOP_LO>(x[k], e[k]);
-    f64_recurse_staged<NTOP_LO, 0, NBAR, W, CH, K>(f, tx, e, j, out, stg, lane);
+    f64_recurse_staged<NTOP_LO, 0, NBAR, W, CH, K, INT>(f, tx, e, j, out, stg, lane);
   }
 }
 
@@ -326,10 +468,12 @@ __device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const
     ok = ok && sig64_chain_ok<NMAX>(x[k]);
   }
   if (__all_sync(0xffffffffu, ok)) {
+    // the first chunk of CH orders and the partial last one unrolled, the
+    // whole chunks between them in a loop (as in f64_recurse_staged)
     Sig64Chain ch[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) ch[k].start(f[k], y[k]);
-    static_for<0, W, 1>([&](auto mc) {
+    auto unrolled = [&](auto mc) {
       constexpr int m = decltype(mc)::value;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -337,7 +481,20 @@ __device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const
         stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + m % CH] = f[k];
       }
       if constexpr (m % CH == CH - 1 || m == NMAX) f64_stage_flush<W, CH, K, m % CH + 1>(out, stg, m - m % CH, j, lane);
-    });
+    };
+    constexpr int CF = W / CH - 1;  // highest whole chunk
+    static_for<0, (W < CH ? W : CH), 1>(unrolled);
+#pragma unroll 1
+    for (int c = 1; c <= CF; ++c) {
+      const int m0 = c * CH;
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + i] = ch[k].next_rt(m0 + i);
+      }
+      f64_stage_flush<W, CH, K, CH>(out, stg, m0, j, lane);
+    }
+    static_for<(CF + 1 > 1 ? CF + 1 : 1) * CH, W, 1>(unrolled);
     return;
   }
   static_for<0, W, 1>([&](auto mc) {

@@ -11,6 +11,10 @@
 // the exact chain from F_0 and 1/x, against 2m roundings for the double
 // chain.
 //
+// The downward recursion of Eq. "r", F_{m-1} = (2x F_m + e^{-x}) / (2m - 1),
+// has only positive terms, so it runs the same way: a product, an aligned
+// sum and a product with the constant 1/(2m - 1) per order.
+//
 // Everything here is plain integer arithmetic, valid on the host too.
 #pragma once
 
@@ -45,9 +49,10 @@ BOYS_HD uint64_t mulhi_trunc(uint64_t a, uint64_t b) {
   return (uint64_t)a1 * b1 + (u >> 32) + (v >> 32);
 }
 
-// The significand and exponent of a positive normal double, from its bits.
+// The significand and exponent of the magnitude of a normal double, from its
+// bits (the sign is ignored).
 BOYS_HD uint64_t sig64_of_bits(uint64_t bits) { return (bits << 11) | (1ull << 63); }
-BOYS_HD int exp_of_bits(uint64_t bits) { return (int)(bits >> 52) - 1023; }
+BOYS_HD int exp_of_bits(uint64_t bits) { return (int)((bits >> 52) & 0x7ff) - 1023; }
 
 // The product of two Sig64 numbers: (s_a, e_a) (s_b, e_b) -> (s, e).
 // mulhi_trunc gives t in [2^62, 2^64), the product being t 2^(e_a + e_b - 62);
@@ -57,6 +62,23 @@ BOYS_HD void sig64_mul(uint64_t &s, int &e, uint64_t sb, int eb) {
   const int top = (int)(t >> 63);
   s = top ? t : t << 1;
   e += eb + top;
+}
+
+// The sum of two Sig64 numbers: (s_a, e_a) + (s_b, e_b) -> (s, e).  The
+// smaller is shifted to the larger's exponent (truncated; by 63 at most, so a
+// negligible one adds a unit of 2^-63 relative), and a carry out of the
+// 64-bit sum is shifted back in.  Relative error below 2^-62.
+BOYS_HD void sig64_add(uint64_t &s, int &e, uint64_t sb, int eb) {
+  const int d = e - eb;
+  const uint64_t big = d >= 0 ? s : sb;
+  uint64_t small = d >= 0 ? sb : s;
+  const int ad = d >= 0 ? d : -d;
+  small >>= (ad < 63 ? ad : 63);
+  e = d >= 0 ? e : eb;
+  const uint64_t sum = big + small;
+  const int carry = sum < big;
+  s = carry ? (sum >> 1) | (1ull << 63) : sum;
+  e += carry;
 }
 
 // The bits of the double nearest s 2^(e - 63) (ties away from zero), for a
@@ -90,6 +112,24 @@ BOYS_HD_CONSTEXPR Sig64 half_odd_product(int m) {
     e += r - 1;  // (k - 1/2) = (2k - 1) / 2
   }
   return Sig64{s, e};
+}
+
+// 1/d for an odd d >= 1 as a Sig64, rounded to nearest: for d >= 3, with
+// 2^(k-1) < d < 2^k, s = round(2^(63+k) / d) by long division (the leading
+// quotient bit of 2^(63+k) is 0) and e = -k.
+BOYS_HD_CONSTEXPR Sig64 recip_odd(int d) {
+  if (d == 1) return Sig64{1ull << 63, 0};
+  int k = 0;
+  while ((1 << k) < d) ++k;
+  uint64_t q = 0, r = 1;  // dividend: a one followed by 63 + k zeros
+  for (int i = 0; i < 63 + k; ++i) {
+    r <<= 1;
+    const uint64_t bit = r >= (uint64_t)d ? 1 : 0;
+    r -= bit * (uint64_t)d;
+    q = (q << 1) | bit;
+  }
+  if (2 * r >= (uint64_t)d) ++q;
+  return Sig64{q, -k};
 }
 
 // The bits of a bound x_max below which the integer chain gives every F_m,

@@ -4,9 +4,11 @@ Counts follow the method (Sec. 2) as the double kernels evaluate it: below the
 cut-off one evaluation of Q~ in root-product form, one division u/v, one
 exponential (shared with the recursion, Eq. "r"), the half-integer powers
 Q^{n+1/2} and D^{-(n+1/2)} as square-and-multiply plus a reciprocal square
-root each, and two operations per step of the downward recursion; above it
-(Eq. "limf1") one reciprocal square root, F_0 and 1/x, the upward product
-chain running on the integer pipes.  "fma" counts every add, multiply or
+root each, and two operations per step of the downward recursion (on the
+integer pipes instead in the row kernels, and for recursions of up to 18
+steps elsewhere); above it (Eq.
+"limf1") one reciprocal square root, F_0 and 1/x, the upward product chain
+running on the integer pipes.  "fma" counts every add, multiply or
 fused multiply-add (each one FP64-pipe instruction).  Bytes per argument are
 the input value plus the n_max+1 outputs.
 """
@@ -80,15 +82,33 @@ def int_chain_orders(n_max: int) -> int:
     return n_max
 
 
-def f64_counts(n_max: int, n_top: int, int_chain: bool = True) -> tuple[dict, dict]:
+# The kernels run the downward recursion on 64-bit integer significands when
+# it unrolls at most this many steps (f64_int_recursion in csrc/boys_f64.cuh),
+# and always in the one-point row kernels from n_max = 12 on, which stage
+# their rows and loop over chunks of orders.
+INT_RECURSION_MAX_STEPS = 18
+STAGED_ROWS_FROM = 12
+
+
+def int_recursion(steps: int, n_max: int | None = None) -> bool:
+    """Whether a recursion of this many steps runs on the integer pipes; with
+    n_max given, in the row kernel of that order, else in an unstaged one
+    (the fused contraction and the gradient)."""
+    return steps <= INT_RECURSION_MAX_STEPS or (n_max is not None and n_max >= STAGED_ROWS_FROM)
+
+
+def f64_counts(n_max: int, n_top: int, int_chain: bool = True, rows: bool = True) -> tuple[dict, dict]:
     """(below-cut-off, above-cut-off) FP64 operation counts per argument, in
-    the form the double kernels evaluate them: the closed form at n_top, one
-    exponential and two operations per step of the downward recursion (Eq.
-    "r") below the cut-off; the asymptote above it (its chain on the integer
-    pipes unless int_chain is False)."""
+    the form the double kernels evaluate them: the closed form at n_top and
+    one exponential below the cut-off, plus two operations per step of the
+    downward recursion (Eq. "r") where it runs in FP64; the asymptote above
+    it.  rows: the row kernel (else an unstaged epilogue kernel).  With
+    int_chain False, the recursion and the asymptote's chain are both
+    counted in FP64 (the all-FP64 kernel)."""
     below = _closed_form_counts(n_top)
     below["exp"] = 1
-    below["fma"] += 2 * n_top  # recursion
+    if not (int_chain and int_recursion(n_top, n_max if rows else None)):
+        below["fma"] += 2 * n_top  # recursion
     return below, _asymptote_counts(n_max, int_chain)
 
 
@@ -102,7 +122,9 @@ def f64_counts_two_point(n_max: int, n_top: int, n_bar: int, n_top_lo: int,
     for k in below:
         below[k] += lo[k]
     below["exp"] = 1
-    below["fma"] += 2 * (n_top - (n_bar + 1)) + 2 * n_top_lo
+    steps = (n_top - (n_bar + 1)) + n_top_lo
+    if not (int_chain and int_recursion(steps)):  # the two-point rows keep the step rule
+        below["fma"] += 2 * steps
     return below, _asymptote_counts(n_max, int_chain)
 
 
@@ -113,7 +135,7 @@ def f64_counts_contract(n_max: int, n_top: int, uniform: bool = True, int_chain:
     contraction of the asymptote as a polynomial in y = 1/x (Horner, n_max
     fused multiply-adds, y and two products), else the asymptote row and the
     dot product."""
-    below, above = f64_counts(n_max, n_top, int_chain)
+    below, above = f64_counts(n_max, n_top, int_chain, rows=False)
     below["fma"] += n_max + 1
     if uniform and n_max <= 16:
         # y = rs^2 (n_max <= 12) or 1/x, needed only from n_max = 1 on

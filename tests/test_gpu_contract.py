@@ -72,16 +72,20 @@ def test_matches_rows_then_dot(lib):
     assert ((fused - ref).abs() / scale).max().item() <= 4e-15
 
 
-@pytest.mark.parametrize("n_max", [12, 23, 36])
+@pytest.mark.parametrize("n_max", [12, 16, 23, 36])
 @pytest.mark.parametrize("count", [5000, (1 << 20) + 3001])
 def test_one_hot_contraction_equals_rows_bitwise(lib, n_max, count):
     # The contraction keeps each row in registers, the row store at n_max >= 12
     # stages it through shared memory: with c = e_m the contraction adds exact
     # zeros to F_m, so both paths must give the same bits (small and large
-    # launch shapes, both lists of a tile, ragged tails).
+    # launch shapes, both lists of a tile, ragged tails) wherever they share
+    # the recursion's arithmetic.  The staged rows always recurse on integer
+    # significands; the contraction does so for up to 18 steps and in FP64
+    # beyond (n_max >= 17), where the two agree to the FP64 recursion's
+    # rounding (below 2.2e-15 relative over 40 steps).
     import torch
 
-    from paper_2504_07637_gb300 import workloads
+    from paper_2504_07637_gb300 import roofline, workloads
 
     x = torch.from_numpy(np.concatenate([workloads.scale(count - 3, seed=n_max), [0.0, 1e-300, 1e8]])).cuda()
     rows = lib.boys(x, n_max)
@@ -92,7 +96,11 @@ def test_one_hot_contraction_equals_rows_bitwise(lib, n_max, count):
         c = torch.zeros((count, n_max + 1), dtype=torch.float64, device="cuda")
         c[:, m] = 1.0
         got = lib.boys_contract(x, n_max, c)
-        assert torch.equal(got, rows[:, m]), m
+        if roofline.int_recursion(lib.top_order_f64(n_max)):
+            assert torch.equal(got, rows[:, m]), m
+        else:
+            ref = rows[:, m]
+            assert ((got - ref).abs() <= 4e-15 * ref.abs()).all().item(), m
 
 
 @pytest.mark.parametrize("n_max", [0, 8, 13, 16])

@@ -54,9 +54,9 @@ def test_square_multiply_counts():
 
 def test_two_point_is_two_closed_forms_and_two_recursions():
     n_max, n_top, n_bar, n_top_lo = 36, 40, 18, 20
-    one, above1 = roofline.f64_counts(n_max, n_top)
-    lo, _ = roofline.f64_counts(n_bar, n_top_lo)
-    two, above2 = roofline.f64_counts_two_point(n_max, n_top, n_bar, n_top_lo)
+    one, above1 = roofline.f64_counts(n_max, n_top, int_chain=False)
+    lo, _ = roofline.f64_counts(n_bar, n_top_lo, int_chain=False)
+    two, above2 = roofline.f64_counts_two_point(n_max, n_top, n_bar, n_top_lo, int_chain=False)
     assert above1 == above2
     assert two["exp"] == 1
     assert two["rsqrt"] == one["rsqrt"] + lo["rsqrt"] and two["div"] == one["div"] + lo["div"]
@@ -91,3 +91,22 @@ def test_asymptote_chain_leaves_the_fp64_pipe():
         assert a64["fma"] - a["fma"] == 2 * n_max == 2 * roofline.int_chain_orders(n_max)
         assert a["fma"] == 1 + (1 if 1 <= n_max <= 12 else 0) and a["rsqrt"] == 1
         assert a["div"] == a64["div"] == (1 if n_max > 12 else 0)
+
+
+def test_integer_recursion_threshold_matches_the_kernels():
+    # the kernels' rule (csrc/boys_f64.cuh) and the model's are the same
+    import re
+
+    src = open(os.path.join(os.path.dirname(roofline.__file__), "csrc", "boys_f64.cuh")).read()
+    m = re.search(r"constexpr bool f64_int_recursion\(int steps\) \{ return steps <= (\d+); \}", src)
+    assert m and int(m.group(1)) == roofline.INT_RECURSION_MAX_STEPS
+    # in the row kernels every recursion leaves the FP64 pipe (from n_max = 12
+    # on they loop over chunks of orders); in the unstaged epilogue kernels
+    # only those of up to 18 steps
+    for n_max, n_top in ((8, 9), (16, 18), (17, 19), (36, 40)):
+        b, _ = roofline.f64_counts(n_max, n_top)
+        b64, _ = roofline.f64_counts(n_max, n_top, int_chain=False)
+        assert b64["fma"] - b["fma"] == 2 * n_top
+        e, _ = roofline.f64_counts(n_max, n_top, rows=False)
+        assert b64["fma"] - e["fma"] == (2 * n_top if n_top <= 18 else 0)
+    assert "f64_recurse_staged<NTOP, 0, NMAX, W, CH, K, true>" in src
