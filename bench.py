@@ -627,6 +627,13 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
             return sum((fb * below[k] + (1 - fb) * above[k]) / rates[k] for k in ("fma", "div", "sqrt", "exp", "rsqrt"))
 
         t_arg = t_per_arg(True)
+        if wl.get("two_point"):
+            n_bar = n_max // 2
+            int_rec = roofline.int_recursion(n_top - n_bar - 1 + lib.boys_top_order_f64(n_bar))
+        else:
+            int_rec = roofline.int_recursion(n_top, n_max)
+        rec_note = ("and the downward recursion run on the integer pipes and are not counted" if int_rec else
+                    "runs on the integer pipes and is not counted; the downward recursion stays in FP64")
         achieved = t_arg * rates["fma"] * count / (ms / 1e3) / 1e12
         achieved64 = t_per_arg(False) * rates["fma"] * count / (ms / 1e3) / 1e12
         peak = rates["fma"] / 1e12
@@ -639,11 +646,12 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
             "traffic": None if wl.get("two_point") else traffic_record(f"f64_split_kernel<{n_max}>/scale_2^26"),
             "note": "FP64-pipe instruction equivalents per second (1 per add/mul/fma; exp, sqrt, rsqrt and div "
             "weighted by their measured cost) vs the DFMA rate measured in this run; the asymptote's upward "
-            f"product chain ({roofline.int_chain_orders(n_max)} orders) runs on the integer pipes and is not "
-            f"counted; {fb:.3f} of arguments below z_{{{n_top},53}}",
+            f"product chain ({roofline.int_chain_orders(n_max)} orders) {rec_note}; "
+            f"{fb:.3f} of arguments below z_{{{n_top},53}}",
             "all_fp64": {"achieved": round(achieved64, 5), "frac": round(achieved64 / peak, 4),
-                         "note": "the same evaluation with the asymptote's chain as two FP64 multiplications per "
-                         "order: the bound of an all-FP64 kernel (above 1: faster than that bound)"},
+                         "note": "the same evaluation with the recursion and the asymptote's chain as two FP64 "
+                         "operations per order: the bound of an all-FP64 kernel (above 1: faster than that "
+                         "bound)"},
             "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 4),
                     "peak_source": hbm_src},
             "nominal": {"peak": F64_NOMINAL_TFMA, "frac": round(achieved / F64_NOMINAL_TFMA, 4),
