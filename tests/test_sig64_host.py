@@ -1,8 +1,10 @@
-"""The integer significand arithmetic of the asymptote's product chain
-(csrc/boys_sig64.cuh), compiled for the host and checked against exact
-integer and rational arithmetic: the truncated 64 x 64 high product, the
-rounding of a significand to a double, the constants prod_{k<=m} (k - 1/2)
-and the bound below which every F_m of the chain is a normal double."""
+"""The integer significand arithmetic of the FP64 kernels' downward recursion
+and asymptote chain (csrc/boys_sig64.cuh), compiled for the host and checked
+against exact integer and rational arithmetic (the truncated 64 x 64 high
+product, the rounding of a significand to a double, the constants
+prod_{k<=m} (k - 1/2) and 1/(2m - 1), the bound below which every F_m of the
+chain is a normal double), and, composed as the kernels compose it, against
+the oracle."""
 import math
 import os
 import shutil
@@ -38,6 +40,34 @@ int main() {
     } else if (op[0] == 'x') {  // x n: sig64_chain_xmax_bits
       std::scanf("%d", &e);
       std::printf("%llu\n", (unsigned long long)sig64_chain_xmax_bits(e));
+    } else if (op[0] == 'd') {  // d top x_bits f_bits e_bits: F_top-1 .. F_0 by the integer recursion
+      unsigned long long xb, fb, eb;
+      std::scanf("%d %llu %llu %llu", &e, &xb, &fb, &eb);
+      const unsigned long long tb = xb + (1ull << 52);  // 2x as the kernels form it
+      uint64_t sf = sig64_of_bits(fb), sx = sig64_of_bits(tb), se = sig64_of_bits(eb);
+      int ef = exp_of_bits(fb), ex = exp_of_bits(tb), ee = exp_of_bits(eb);
+      for (int m = e; m >= 1; --m) {
+        sig64_mul(sf, ef, sx, ex);
+        sig64_add(sf, ef, se, ee);
+        const Sig64 k = recip_odd(2 * m - 1);
+        sig64_mul(sf, ef, k.s, k.e);
+        std::printf("%llu ", (unsigned long long)sig64_round_bits(sf, ef));
+      }
+      std::printf("\n");
+    } else if (op[0] == 'c') {  // c n f0_bits y_bits: F_1 .. F_n by the integer chain
+      unsigned long long fb, yb;
+      std::scanf("%d %llu %llu", &e, &fb, &yb);
+      uint64_t s = sig64_of_bits(fb), sy = sig64_of_bits(yb);
+      int es = exp_of_bits(fb), ey = exp_of_bits(yb);
+      for (int m = 1; m <= e; ++m) {
+        sig64_mul(s, es, sy, ey);
+        const Sig64 h = half_odd_product(m);
+        uint64_t w = s;
+        int ew = es;
+        sig64_mul(w, ew, h.s, h.e);
+        std::printf("%llu ", (unsigned long long)sig64_round_bits(w, ew));
+      }
+      std::printf("\n");
     }
   }
 }
@@ -116,3 +146,69 @@ def test_chain_bound_keeps_every_order_normal(run):
         log2_fn = math.log2(c_n) - (n + 0.5) * math.log2(xmax)
         assert log2_fn > -1022, n
         assert 1.0 / xmax > np.finfo(np.float64).tiny
+
+
+def _bits(v):
+    return struct.unpack("<Q", struct.pack("<d", float(v)))[0]
+
+
+def test_reciprocals_of_odd_numbers(run):
+    # At x = 0 each step of the recursion is F_{k-1} = e^{-0} / (2k - 1): the
+    # 2x F_k term (2x is 2^-1022 as the kernels form it) shifts out of the sum,
+    # so every output is the constant 1/(2k - 1) times 1, rounded once, and
+    # must be the correctly rounded double 1/(2k - 1), for k up to 41.
+    lines = [f"d {m} {_bits(0.0)} {_bits(1.0 / (2 * m + 1))} {_bits(1.0)}" for m in range(1, 42)]
+    for m, line in zip(range(1, 42), run(lines)):
+        got = [_double(int(t)) for t in line.split()]
+        want = [1.0 / (2 * k - 1) for k in range(m, 0, -1)]
+        assert got == want, m
+
+
+@pytest.mark.parametrize("top", [9, 18, 40])
+def test_integer_recursion_against_the_oracle(run, oracle_mod, top):
+    """The downward recursion (Eq. "r") on integer significands, from F_top and
+    e^{-x} rounded to doubles as the kernels have them.  Each step is a
+    weighted mean of the relative errors of F_m and e^{-x} (both terms are
+    positive), so F_m carries at most the larger input rounding (2^-53) plus
+    its own (2^-53) and the integer steps' truncation (below 2^-61 each):
+    within 2.05 units of 2^-53 of the oracle's long double value.  The same
+    recursion in double drifts further."""
+    rng = np.random.default_rng(top)
+    x = np.concatenate([[0.0, 5e-324, 1e-310, 1e-300, 1e-16], rng.uniform(0.0, 118.0, 3000),
+                        np.exp(rng.uniform(-20, math.log(118.0), 1000))])
+    ref = oracle_mod.boys_ld(x, top)  # F_0 .. F_top in long double
+    ftop = ref[:, top].astype(np.float64)
+    e = np.exp(-x)
+    lines = [f"d {top} {_bits(v)} {_bits(f)} {_bits(ev)}" for v, f, ev in zip(x, ftop, e)]
+    got = np.array([[_double(int(t)) for t in line.split()][::-1] for line in run(lines)])  # F_0 .. F_top-1
+    rel = (np.abs(got - ref[:, :top]) / ref[:, :top]).astype(np.float64)
+    assert rel.max() <= 2.05 * 2.0**-53, (top, rel.max() / 2.0**-53)
+    # the same steps in double, for comparison
+    f = ftop.copy()
+    worst64 = 0.0
+    for m in range(top, 0, -1):
+        f = (2.0 * x * f + e) * (1.0 / (2 * m - 1))
+        worst64 = max(worst64, float(np.max(np.abs(f - ref[:, m - 1]) / ref[:, m - 1])))
+    assert rel.max() <= worst64
+
+
+@pytest.mark.parametrize("n", [1, 8, 12, 16, 36])
+def test_integer_chain_against_the_oracle(run, oracle_mod, n):
+    """The asymptote's upward chain (Eq. "limf1") on integer significands from
+    F_0 = c_0 / sqrt(x) and y = 1/x as doubles, for x above the cut-off and
+    below the chain's range bound: F_m = F_0 y^m prod (k - 1/2) carries F_0's
+    error (three roundings here), m times that of y (one rounding), its own
+    rounding and the asymptote's distance from F_m (below 2^-53 above z): within
+    3.5 + m units of 2^-53 of the oracle's long double value."""
+    rng = np.random.default_rng(100 + n)
+    xmax = _double(int(run([f"x {n}"])[0]))
+    z = oracle_mod.cutoff(n, 53)
+    x = np.exp(rng.uniform(math.log(z), math.log(min(xmax, 1e300)) - 1e-9, 2000))
+    f0 = 0.88622692545275801365 / np.sqrt(x)
+    y = 1.0 / x
+    lines = [f"c {n} {_bits(a)} {_bits(b)}" for a, b in zip(f0, y)]
+    got = np.array([[_double(int(t)) for t in line.split()] for line in run(lines)])  # F_1 .. F_n
+    ref = oracle_mod.boys_ld(x, n)[:, 1:]
+    rel = (np.abs(got - ref) / ref).astype(np.float64)
+    bound = (3.5 + np.arange(1, n + 1)) * 2.0**-53
+    assert np.all(rel.max(axis=0) <= bound), (rel.max(axis=0) / 2.0**-53)
