@@ -4,10 +4,14 @@
 // the FP64 pipe, not by HBM: every design choice below removes FP64
 // instructions.
 //  * Compaction: each tile of arguments is split into a below-cut-off list
-//    (closed form, ~95 FP64 operations) and an above-cut-off list (asymptote,
-//    ~25), and warps take 32 entries of one list at a time, so no warp pays
-//    for both branches (with arguments mixed at random, nearly every warp of a
-//    plain one-argument-per-thread kernel would).
+//    (closed form: at n_max = 8 about 50 FP64 operations, a division, an
+//    exponential and two reciprocal square roots) and an above-cut-off list
+//    (asymptote), and warps take 32 entries of one list at a time, so no warp
+//    pays for both branches (with arguments mixed at random, nearly every
+//    warp of a plain one-argument-per-thread kernel would).
+//  * The downward recursion and the asymptote's upward product chain run on
+//    64-bit integer significands (boys_sig64.cuh), on integer pipes that an
+//    FP64-bound kernel leaves idle; the FP64 pipe keeps the closed form.
 //  * Classification, the factor 2 of the recursion and the final scaling of
 //    the exponential are integer operations on the bit patterns.
 //  * e^{-x} is Tang's table-driven method (ACM TOMS 15(2), 1989): 2^(k/64)
