@@ -44,6 +44,29 @@ int boys_microbench_ops_per_thread_iter(void);
  * the GPU's ceiling rather than a latency limit.  Returns a boys_status. */
 int boys_microbench_dfma(int chains, int64_t iters, double *sink, int blocks, void *stream);
 
+/* Integer-pipe kinds for boys_microbench_int.  The downward recursion and the
+ * asymptote's chain of the double path run on 64-bit integer significands
+ * (32 x 32 -> 64-bit multiply-adds, 64-bit adds and shifts); these measure
+ * how fast the GPU retires such instructions, for a ceiling that counts the
+ * integer pipes beside the FP64 pipe. */
+enum {
+    BOYS_MICRO_INT_MADWIDE = 0, /* mad.wide.u32: 32 x 32 -> 64-bit multiply-add */
+    BOYS_MICRO_INT_MADLO = 1,   /* mad.lo.u32: 32-bit multiply-add */
+    BOYS_MICRO_INT_ALU = 2,     /* add.u32 then xor.b32 (two instructions per chain step) */
+    BOYS_MICRO_INT_SHIFT64 = 3  /* 64-bit shift by a run-time amount, then a 64-bit or */
+};
+
+/* Launch `blocks` x 256 threads, each running `iters` steps of 8 independent
+ * chains of integer kind `kind` (BOYS_MICRO_INT_*) on `stream`.  `sink` is a
+ * device double, written only if a 64-bit checksum of the chains takes one
+ * particular value (in practice never).  Returns a boys_status
+ * (BOYS_ERR_ARG for an unknown kind). */
+int boys_microbench_int(int kind, int64_t iters, double *sink, int blocks, void *stream);
+
+/* PTX instructions per chain step of an integer kind (-1 if unknown); the
+ * pipe each one lands on is measured, not assumed. */
+int boys_microbench_int_insts_per_chain_iter(int kind);
+
 /* out[i] = e^{-x[i]} by the library's own exponential (Tang's table-driven
  * method), for testing it against a reference; valid for 0 <= x <= 700.
  * x, out: device arrays of n doubles.  Returns a boys_status. */

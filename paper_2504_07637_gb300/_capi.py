@@ -51,6 +51,8 @@ SIGNATURES = {
     "boys_microbench_launch": (c_int, [c_int, i64, vp, c_int, vp]),
     "boys_microbench_ops_per_thread_iter": (c_int, []),
     "boys_microbench_dfma": (c_int, [c_int, i64, vp, c_int, vp]),
+    "boys_microbench_int": (c_int, [c_int, i64, vp, c_int, vp]),
+    "boys_microbench_int_insts_per_chain_iter": (c_int, [c_int]),
     "boys_debug_exp_neg": (c_int, [vp, i64, vp, vp]),
 }
 

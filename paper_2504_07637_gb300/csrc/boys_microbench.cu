@@ -115,6 +115,82 @@ extern "C" int boys_microbench_dfma(int chains, int64_t iters, double *sink, int
 }
 
 namespace {
+
+// Integer-pipe chains: per thread 8 independent chains of one instruction
+// kind, written as inline PTX so that the front end cannot fold them.  The
+// counted unit is the warp instruction; which pipe each kind occupies is
+// read from ncu's per-pipe instruction counters, not assumed.
+template <int KIND>
+__global__ void __launch_bounds__(256) micro_int_kernel(int64_t iters, uint32_t k1, uint32_t k2, double *sink) {
+  uint32_t a[kChains];
+  uint64_t w[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) {
+    a[c] = threadIdx.x * 0x9e3779b9u + 17u * c + 1u;
+    w[c] = ((uint64_t)a[c] << 17) | c;
+  }
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+      if constexpr (KIND == BOYS_MICRO_INT_MADWIDE) {
+        // w = lo(w) k1 + w: one 32 x 32 -> 64-bit multiply-add
+        asm("{\n\t.reg .u32 l, h;\n\tmov.b64 {l, h}, %0;\n\tmad.wide.u32 %0, l, %1, %0;\n\t}" : "+l"(w[c]) : "r"(k1));
+      }
+      if constexpr (KIND == BOYS_MICRO_INT_MADLO) {
+        asm("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a[c]) : "r"(k1), "r"(k2));
+      }
+      if constexpr (KIND == BOYS_MICRO_INT_ALU) {
+        // an add and an exclusive or alternate, so no two fuse into one
+        // three-input instruction
+        asm("add.u32 %0, %0, %1;\n\txor.b32 %0, %0, %2;" : "+r"(a[c]) : "r"(k1), "r"(k2));
+      }
+      if constexpr (KIND == BOYS_MICRO_INT_SHIFT64) {
+        // 64-bit shift by a run-time amount, then an or: the aligned sum's shift
+        asm("{\n\t.reg .u64 t;\n\tshr.b64 t, %0, %1;\n\tor.b64 %0, t, %2;\n\t}"
+            : "+l"(w[c])
+            : "r"(k1 & 7u), "l"((uint64_t)k2 << 40));
+      }
+    }
+  }
+  // a 64-bit mix of every chain (a plain sum of 32-bit values has a range
+  // the compiler can bound, and would drop the chains as dead code)
+  uint64_t acc = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) acc = (acc ^ a[c] ^ w[c]) * 0x9e3779b97f4a7c15ull;
+  if (acc == 0x123456789abcdefull) sink[0] = (double)acc;  // (practically) never true; keeps the chains live
+}
+
+template <int KIND>
+int launch_int(int64_t iters, double *sink, int blocks, cudaStream_t s) {
+  micro_int_kernel<KIND><<<blocks, 256, 0, s>>>(iters, 0x9e3779b1u, 0x7f4a7c15u, sink);
+  return cudaPeekAtLastError() == cudaSuccess ? BOYS_OK : BOYS_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" int boys_microbench_int(int kind, int64_t iters, double *sink, int blocks, void *stream) {
+  if (iters < 0 || blocks < 1 || !sink) return BOYS_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (kind) {
+    case BOYS_MICRO_INT_MADWIDE: return launch_int<BOYS_MICRO_INT_MADWIDE>(iters, sink, blocks, s);
+    case BOYS_MICRO_INT_MADLO: return launch_int<BOYS_MICRO_INT_MADLO>(iters, sink, blocks, s);
+    case BOYS_MICRO_INT_ALU: return launch_int<BOYS_MICRO_INT_ALU>(iters, sink, blocks, s);
+    case BOYS_MICRO_INT_SHIFT64: return launch_int<BOYS_MICRO_INT_SHIFT64>(iters, sink, blocks, s);
+    default: return BOYS_ERR_ARG;
+  }
+}
+
+extern "C" int boys_microbench_int_insts_per_chain_iter(int kind) {
+  switch (kind) {
+    case BOYS_MICRO_INT_MADWIDE: return 1;
+    case BOYS_MICRO_INT_MADLO: return 1;
+    case BOYS_MICRO_INT_ALU: return 2;
+    case BOYS_MICRO_INT_SHIFT64: return 2;
+    default: return -1;
+  }
+}
+
+namespace {
 __global__ void exp_neg_kernel(const double *__restrict__ x, int64_t n, double *__restrict__ out) {
   __shared__ double tab64[64];
   if (threadIdx.x < 64) tab64[threadIdx.x] = boys::kExp2Frac64[threadIdx.x];
