@@ -37,6 +37,8 @@ WORKLOADS = {
     # the float path on the same arguments rounded to float
     "scale_f32_n8": dict(count=1 << 26, n_max=8, dtype="f32"),
     "scale_f32_n16": dict(count=1 << 26, n_max=16, dtype="f32"),
+    "scale_f32_n36": dict(count=1 << 24, n_max=36, dtype="f32"),
+    "scale_f32_n36_small": dict(count=1 << 22, n_max=36, dtype="f32"),
     # 4096 ragged requests (counts log-uniform on [64, 65536], n_max uniform on 0..16), graph replays
     "ragged_f64": dict(count=0, n_max=16, dtype="f64", kind="ragged"),
     # differentiation: 2^24 arguments, forward to n_max = 9, backward of sum_{m<=8} w_m F_m
@@ -152,8 +154,12 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-def oracle_rate(x_all, n_max: int, target_cpu_s: float = 15.0, budget_s: float = 30.0):
-    """Time the CPU oracle on a bounded sample on all host cores."""
+def oracle_rate(x_all, n_max: int, target_cpu_s: float = 15.0, budget_s: float = 30.0, rows=None, dtype="f64"):
+    """Time the CPU oracle on a bounded sample on all host cores.
+
+    With rows (the benchmark's own output on the device, [count, n_max+1]),
+    the oracle's values for the sample also measure the error of those rows:
+    returns (baseline, accuracy)."""
     import numpy as np
 
     import oracle
@@ -168,15 +174,44 @@ def oracle_rate(x_all, n_max: int, target_cpu_s: float = 15.0, budget_s: float =
     sample = int(min(sample, budget_s * cores / per))
     xs = np.ascontiguousarray(x_all[:sample])
     t0 = time.perf_counter()
-    oracle.boys_threaded(xs, n_max, cores)
+    ref = oracle.boys_threaded(xs, n_max, cores)
     dt = time.perf_counter() - t0
-    return {
+    base = {
         "value": round(sample * (n_max + 1) / dt / 1e9, 6),
         "unit": "G F_m values/s",
         "cores": cores,
         "kind": "oracle",
         "sample": f"first {sample} arguments of the same workload, n_max={n_max}, long double, "
         f"{cores} host threads, {dt:.2f} s wall",
+    }
+    if rows is None:
+        return base, None
+    return base, row_errors(rows[:sample].cpu().numpy().astype(np.float64), ref, dtype, sample)
+
+
+def row_errors(got, ref, dtype, sample):
+    """Maximum relative error per m of the rows against the oracle, with the
+    tolerance of the path (FP64 2e-14, FP32 2e-6 for every m).  Where the
+    exact value is below the smallest normal number of the output type the
+    test is absolute (2 subnormal units for double; 2e-6 |F| + 2^-149 for
+    float)."""
+    import numpy as np
+
+    tiny, sub = (np.finfo(np.float32).tiny, 2.0 ** -149) if dtype == "f32" else (np.finfo(np.float64).tiny, 2.0 ** -1073)
+    normal = np.abs(ref) >= tiny
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rel = np.where(normal, np.abs(got - ref) / np.where(normal, np.abs(ref), 1.0), 0.0)
+    small_ok = bool(np.all(normal | (np.abs(got - ref) <= TOL[dtype] * np.abs(ref) + sub)))
+    finite = bool(np.all(np.isfinite(got)))
+    per_m = [float(v) for v in rel.max(axis=0)]
+    worst = max(per_m) if per_m else 0.0
+    return {
+        "max_rel_err_per_m": [float(f"{v:.3g}") for v in per_m],
+        "max_rel_err": float(f"{worst:.3g}"),
+        "tolerance": TOL[dtype],
+        "pass": bool(worst <= TOL[dtype] and small_ok and finite),
+        "how": f"the benchmark's own output rows for its first {sample} arguments against the CPU oracle "
+        f"(long double), every m",
     }
 
 
@@ -266,6 +301,27 @@ def microbench(capi, device):
     t_fma = 1.0 / rates["fma"]
     for k in ("exp_cuda", "exp", "sqrt", "rsqrt", "div"):
         rates[k] = 1.0 / max(1.0 / rates[k] - t_fma, 1e-30)
+    # integer pipes, in warp instructions per second: the 32-bit multiply-add
+    # chain (fmaheavy pipe) and the 64-bit shift chain (ALU pipe); how many
+    # instructions of that pipe one chain step issues was counted by ncu
+    micro = pipes_micro()
+    warps = blocks * 256 // 32
+    for name, kind, iters in (("imad", 1, 4096), ("alu", 3, 4096)):
+        per_step = micro.get(name, {}).get("inst_per_chain_step")
+        if not per_step:
+            continue
+        capi.call("boys_microbench_int", kind, 16, sink.data_ptr(), blocks, stream.cuda_stream)
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            capi.call("boys_microbench_int", kind, iters, sink.data_ptr(), blocks, stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            dt = e0.elapsed_time(e1) / 1e3
+            best = dt if best is None else min(best, dt)
+        rates[name + "_warp"] = warps * iters * chains * per_step / best
+    rates["sms"] = sms
     return rates
 
 
@@ -308,6 +364,96 @@ def instruction_record(kernel_key: str):
         with open(os.path.join(ROOT, fn), "rb") as fh:
             h.update(fh.read())
     return rec.get("warp_inst_per_arg") if h.hexdigest() == rec.get("sha256") else None
+
+
+def _pipes():
+    path = os.path.join(ROOT, "profiles", "pipes.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def _sources_sha(files):
+    import hashlib
+
+    h = hashlib.sha256()
+    for fn in files:
+        with open(os.path.join(ROOT, fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def pipes_micro():
+    """The microbenchmarks' instructions per chain step on each pipe (ncu),
+    if the record still matches the microbenchmark's source."""
+    rec = _pipes().get("micro")
+    if not rec or _sources_sha(rec.get("sources", [])) != rec.get("sha256"):
+        return {}
+    return rec
+
+
+def pipe_ceiling(kernel_key, count, seconds, rates, sm_hz):
+    """The ceiling of a kernel over the pipes it uses.
+
+    Per argument, the kernel's work on each pipe comes from one small ncu
+    capture (profiles/pipes.json, valid while its sources are unchanged):
+    FP64-pipe cycles in DFMA warp instructions, ALU-pipe cycles in the ALU
+    microbenchmark's instructions, fmaheavy-pipe cycles in 32-bit
+    multiply-adds, and every issued warp instruction.  Each is divided by
+    its rate measured in this run (the DFMA, ALU and multiply-add chains;
+    issue at one warp instruction per clock per scheduler, 4 per SM, at the
+    sampled SM clock).  The slowest pipe bounds the kernel; frac is that
+    time over the measured one."""
+    rec = _pipes().get(kernel_key)
+    if not rec or _sources_sha(rec.get("sources", [])) != rec.get("sha256"):
+        return None
+    need = ("fma", "alu_warp", "imad_warp", "sms")
+    if rates is None or any(k not in rates for k in need) or not sm_hz:
+        return None
+    w = rec["per_arg"]
+    t = {
+        "fp64": w["fp64_dfma"] * count / (rates["fma"] / 32.0),
+        "alu": w["alu"] * count / rates["alu_warp"],
+        "fmaheavy": w["fmaheavy_imad"] * count / rates["imad_warp"],
+        "issue": w["inst"] * count / (ISSUE_PER_SM_CLOCK * rates["sms"] * sm_hz),
+    }
+    pipe = max(t, key=t.get)
+    rate_g = {"fp64": rates["fma"] / 32e9, "alu": rates["alu_warp"] / 1e9, "fmaheavy": rates["imad_warp"] / 1e9,
+              "issue": ISSUE_PER_SM_CLOCK * rates["sms"] * sm_hz / 1e9}
+    return {
+        "bound_pipe": pipe,
+        "rate_g": {k: round(v, 3) for k, v in rate_g.items()},
+        "frac": round(t[pipe] / seconds, 4),
+        "pipe_ms": {k: round(v * 1e3, 4) for k, v in t.items()},
+        "measured_ms": round(seconds * 1e3, 4),
+        "per_arg": w,
+        "source": rec.get("how", ""),
+    }
+
+
+def apply_ceiling(roof, ceiling):
+    """Make the pipe ceiling the roofline's headline figures, keeping the
+    FP64 op-count model beside it under "fp64_model"."""
+    roof["fp64_model"] = {k: roof[k] for k in ("achieved", "peak", "unit", "frac", "note")}
+    if ceiling is None:
+        roof["ceiling"] = None
+        roof["note"] = ("no current per-pipe profile of this kernel (profiles/pipes.json): headline figures are "
+                        "the FP64 op-count model's; " + roof["note"])
+        return
+    pipe = ceiling["bound_pipe"]
+    t_pipe = ceiling["pipe_ms"][pipe] / 1e3
+    t_meas = ceiling["measured_ms"] / 1e3
+    # the bounding pipe's measured rate, in G warp instructions per second
+    peak = {"fp64": "dfma", "alu": "alu", "fmaheavy": "imad", "issue": "issue"}[pipe]
+    roof["achieved"] = round(t_pipe / t_meas * ceiling["rate_g"][pipe], 3)
+    roof["peak"] = round(ceiling["rate_g"][pipe], 3)
+    roof["unit"] = f"G warp instructions/s on the {pipe} pipe ({peak} rate measured in this run)"
+    roof["frac"] = ceiling["frac"]
+    roof["ceiling"] = ceiling
+    roof["note"] = ("combined ceiling: the kernel's per-argument work on the FP64, ALU and fmaheavy pipes and its "
+                    "issued instructions (ncu, small case), each at its rate measured in this run; the slowest "
+                    f"pipe ({pipe}) bounds the kernel. The FP64 op-count model is under fp64_model.")
 
 
 # GB300 issue rate: 4 warp schedulers per SM, one warp instruction per clock
@@ -569,7 +715,7 @@ def run_grad(args, wl, emit=True):
     return line
 
 
-def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks_index=None):
+def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks_index=None, keep_rows=False):
     """Time one scale-workload configuration; returns its figures.
 
     The timed region is exactly `steps` evaluation calls on the current
@@ -610,6 +756,8 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
     clk = clocks.stop() if clocks else None
     ms = e0.elapsed_time(e1) / steps
     res = {"ms": ms, "values": count * (n_max + 1), "clocks": clk, "x_host": x_host}
+    if keep_rows:
+        res["rows"] = out
     hbm_peak, hbm_src = measured_peaks()
     hbm_gbs = roofline.bytes_per_arg(n_max, esz) * count / (ms / 1e3) / 1e9
     if not f32 and rates is not None:
@@ -637,6 +785,9 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
         achieved = t_arg * rates["fma"] * count / (ms / 1e3) / 1e12
         achieved64 = t_per_arg(False) * rates["fma"] * count / (ms / 1e3) / 1e12
         peak = rates["fma"] / 1e12
+        sm_hz = (clk or {}).get("sm_mhz") or SM_CLOCK_MAX_HZ / 1e6
+        key = f"{'f64_two_point' if wl.get('two_point') else 'f64_rows'}<{n_max}>/scale"
+        ceiling = pipe_ceiling(key, count, ms / 1e3, rates, sm_hz * 1e6)
         res["roofline"] = {
             "bound": "alu",
             "achieved": round(achieved, 5),
@@ -657,8 +808,9 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
             "nominal": {"peak": F64_NOMINAL_TFMA, "frac": round(achieved / F64_NOMINAL_TFMA, 4),
                         "source": "GB300 FP64 1.25 TFLOP/s nominal = 0.625 T FMA/s (2 DFMA per clock per SM at "
                         "152 SMs x 2.07 GHz)"},
-            "measured_rates_gops": {k: round(v / 1e9, 2) for k, v in rates.items()},
+            "measured_rates_gops": {k: round(v / 1e9, 2) for k, v in rates.items() if k != "sms"},
         }
+        apply_ceiling(res["roofline"], ceiling)
     elif f32:
         n_top = _capi.load().boys_top_order_f32(n_max)
         z = _capi.load().boys_cutoff(n_top, 24)
@@ -695,18 +847,54 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
             e2e_step()
             stream.synchronize()
         dt = (time.perf_counter() - t0) / k2
+        h2d_b, d2h_b = esz * count, esz * count * (n_max + 1)
+        link = link_rates(xp, op, device)
+        t_h2d, t_d2h = h2d_b / (link["h2d_gbs"] * 1e9), d2h_b / (link["d2h_gbs"] * 1e9)
         res["e2e"] = {
             "value": round(count * (n_max + 1) / dt / 1e9, 4),
             "unit": "G F_m values/s",
-            "h2d_bytes_per_step": esz * count,
-            "d2h_bytes_per_step": esz * count * (n_max + 1),
+            "h2d_bytes_per_step": h2d_b,
+            "d2h_bytes_per_step": d2h_b,
             "how": f"{fn}_host: pinned host in/out, 256 MiB device workspace, chunked copies overlapped with "
             "compute; host wall clock",
+            # the host link bounds this number: plain pinned copies of the
+            # same buffers, timed in the same run
+            "link_gbs": {"h2d": link["h2d_gbs"], "d2h": link["d2h_gbs"]},
+            "link_frac": round(max(t_h2d, t_d2h) / dt, 4),
+            "link_frac_serial": round((t_h2d + t_d2h) / dt, 4),
+            "link_note": "link_frac: the larger of the two plain copies (both directions at once) over the measured "
+            "step; link_frac_serial: the two copies one after the other",
         }
         del xp, op, wsp
     del x, out
     torch.cuda.empty_cache()
     return res
+
+
+def link_rates(host_in, host_out, device):
+    """Plain pinned host <-> device copy rates (GB/s, best of 3 with CUDA
+    events) for the buffers of the end-to-end run: host_in -> device and
+    device -> host_out."""
+    import torch
+
+    stream = torch.cuda.current_stream(device)
+    dev_in = torch.empty(host_in.shape, dtype=host_in.dtype, device=device)
+    dev_out = torch.empty(host_out.shape, dtype=host_out.dtype, device=device)
+    out = {}
+    for name, dst, src, nbytes in (("h2d_gbs", dev_in, host_in, host_in.numel() * host_in.element_size()),
+                                   ("d2h_gbs", host_out, dev_out, host_out.numel() * host_out.element_size())):
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        out[name] = round(nbytes / best / 1e9, 1)
+    del dev_in, dev_out
+    return out
 
 
 def measure_contract(wl, steps, warmup, device, seed, rates=None):
@@ -875,7 +1063,7 @@ def main():
         dist.barrier()
     rates = None if args.no_extras or wl["dtype"] == "f32" else microbench(_capi, device)
     main_res = measure_scale(wl, args.steps, args.warmup, device, seed, rates=rates, e2e=not args.no_extras,
-                             clocks_index=local)
+                             clocks_index=local, keep_rows=rank == 0 and not args.no_cpu_baseline)
     ms = main_res["ms"]
     ms_max = shard.max_over_ranks(ms, device)
     value = main_res["values"] * ws / (ms_max / 1e3) / 1e9
@@ -890,7 +1078,7 @@ def main():
     if ws == 1 and not args.no_extras and args.workload == "scale_f64_n8":
         suite = {"plain_f64_n8_65536": measure_plain(device, rates)}
         for name in ("scale_f64_n0", "scale_f64_n4", "scale_f64_n16", "scale_f64_n36", "two_point_f64_n36",
-                     "scale_f32_n8", "scale_f32_n16"):
+                     "scale_f32_n8", "scale_f32_n16", "scale_f32_n36"):
             r = measure_scale(WORKLOADS[name], 10, 3, device, seed, rates=rates)
             suite[name] = {"value": round(r["values"] / (r["ms"] / 1e3) / 1e9, 4), "unit": "G F_m values/s",
                            "ms_per_step": round(r["ms"], 4)}
@@ -899,6 +1087,10 @@ def main():
                 suite[name]["roofline_frac"] = r["roofline"]["frac"]
                 if "all_fp64" in r["roofline"]:
                     suite[name]["all_fp64_frac"] = r["roofline"]["all_fp64"]["frac"]
+                if "fp64_model" in r["roofline"]:
+                    suite[name]["fp64_model_frac"] = r["roofline"]["fp64_model"]["frac"]
+                    c = r["roofline"].get("ceiling")
+                    suite[name]["ceiling_pipe"] = c["bound_pipe"] if c else None
         # the float path against the double one on the same arguments and order (n_max = 8)
         suite["scale_f32_n8"]["speedup_vs_f64_n8"] = round(suite["scale_f32_n8"]["value"] / value, 2)
         for name in ("contract_f64_n8", "contract_f32_n8"):
@@ -914,10 +1106,12 @@ def main():
                                                 "backward_speedup_vs_central_difference")}
         suite["grad_f64"]["backward_roofline"] = gr["roofline"]
         extras["workloads"] = suite
+    accuracy = None
     if rank == 0 and not args.no_cpu_baseline:
         import numpy as np
 
-        extras["cpu_baseline"] = oracle_rate(main_res["x_host"].astype(np.float64), n_max)
+        extras["cpu_baseline"], accuracy = oracle_rate(main_res["x_host"].astype(np.float64), n_max,
+                                                        rows=main_res.get("rows"), dtype=wl["dtype"])
     if rank == 0:
         line = {
             "metric": METRIC,
@@ -936,7 +1130,8 @@ def main():
                 "workload": f"{args.workload}: {count} arguments x = p R^2 per GPU ({wl['dtype']}), n_max={n_max}",
                 "global_batch": count * ws,
                 "n_max": n_max,
-                "max_rel_err": TOL[wl["dtype"]],
+                "max_rel_err": accuracy["max_rel_err"] if accuracy else "not measured (--no-cpu-baseline)",
+                "accuracy": accuracy,
                 "l2": "inputs and outputs larger than the 129 MB L2; no flush needed",
                 "parallelism": f"dp{ws} (independent shards, no collective)",
             },
@@ -945,8 +1140,12 @@ def main():
             **extras,
         }
         print(json.dumps(line), flush=True)
+    main_res.pop("rows", None)
     if ws > 1:
         dist.destroy_process_group()
+    if accuracy is not None and not accuracy["pass"]:
+        # the metric is values/s at the stated error: a run above it has no value
+        sys.exit(f"bench: measured max relative error {accuracy['max_rel_err']:g} above {accuracy['tolerance']:g}")
 
 
 if __name__ == "__main__":

@@ -81,7 +81,11 @@ int boys_top_order_f32(int n_max);
  * from fits one order above the paper's single-precision column and the
  * error-amplifying steps (q0 + q1 x, Q^{n+1/2}, e^{-x}, D, D^{-(n+1/2)}) in
  * float-float arithmetic (Sec. 3 suggests extra precision for full 24-bit
- * results).
+ * results).  From n_max = 17 on (n_top >= 18), where the amplification
+ * s^2 (T/D) stays large far out in x, the rational part of Q~ and its
+ * coefficients are float-float too, the recursion's constants 1/(2m - 1) are
+ * float pairs and the asymptote's product chain is compensated.
+ * n_max <= boys_max_n(24) = 36.
  *   x:   device, [count] floats
  *   out: device, [count, n_max+1] floats, row-major
  * Max relative error against the exact F_m at the float argument: 2e-6 for
@@ -135,6 +139,8 @@ boys_status boys_eval_f64_two_point(const double *x, int64_t count, int n_max, d
  * contracting the rows by rounding only (a few ulp of sum_m |c_m| F_m). */
 boys_status boys_eval_contract_f64(const double *x, int64_t count, int n_max, const double *c, int64_t c_row,
                                    int64_t c_col, double *out, void *stream);
+/* The float contraction takes n_max <= 16 (else BOYS_ERR_NMAX): its sums and
+ * Horner polynomials are plain FP32. */
 boys_status boys_eval_contract_f32(const float *x, int64_t count, int n_max, const float *c, int64_t c_row,
                                    int64_t c_col, float *out, void *stream);
 
@@ -210,7 +216,11 @@ boys_status boys_eval_ragged_f64(const double *x, int64_t x_size, const int64_t 
  *   - Every call shares the array, which keeps the last call's contents; the
  *     call clears what must start at zero itself.  Calls whose work overlaps
  *     on the GPU race on the array: order them (e.g. one stream).
- * Results are those of boys_eval_ragged_f64. */
+ *   - The count of invalid requests that boys_ragged_errors reads from a
+ *     workspace is not available here (the array's address stays inside the
+ *     library): an invalid request shows only as its output range filled
+ *     with NaN, where that range lies inside [0, out_size).
+ * Results are those of boys_eval_ragged_f64, bit for bit. */
 #define BOYS_RAGGED_NOALLOC_MAX_REQUESTS 65536
 boys_status boys_eval_ragged_f64_noalloc(const double *x, int64_t x_size, const int64_t *offsets, const int32_t *n_max,
                                          const int64_t *out_offsets, int32_t num_requests, double *out,

@@ -32,11 +32,14 @@ int boys_two_point_dispatch_p4(int n_max, const double *x, int64_t count, double
 int boys_grad_saved_launch(const double *F, int64_t ld_F, const double *g, int64_t g_row, int64_t g_col,
                            int64_t count, int n_max, double *grad, cudaStream_t s);
 int boys_f32_dispatch_p1(int n_max, const float *x, int64_t count, float *out, cudaStream_t s);
+int boys_f32_dispatch_p2(int n_max, const float *x, int64_t count, float *out, cudaStream_t s);
+int boys_f32_dispatch_p3(int n_max, const float *x, int64_t count, float *out, cudaStream_t s);
 
 namespace {
 
 using boys::f32_top_order;
 using boys::kMaxNF32;
+using boys::kMaxNF32Contract;
 using boys::kMaxNF64;
 
 // The kernels are built for sm_103a only; reject other devices up front
@@ -119,7 +122,11 @@ int dispatch_f64(int n_max, const double *x, int64_t count, double *out, cudaStr
 }
 
 int dispatch_f32(int n_max, const float *x, int64_t count, float *out, cudaStream_t s) {
-  const int rc = n_max <= 8 ? boys_f32_dispatch_p0(n_max, x, count, out, s) : boys_f32_dispatch_p1(n_max, x, count, out, s);
+  // the order ranges of boys_f32_p0.cu .. boys_f32_p3.cu
+  const int rc = n_max <= 8    ? boys_f32_dispatch_p0(n_max, x, count, out, s)
+                 : n_max <= 16 ? boys_f32_dispatch_p1(n_max, x, count, out, s)
+                 : n_max <= 26 ? boys_f32_dispatch_p2(n_max, x, count, out, s)
+                               : boys_f32_dispatch_p3(n_max, x, count, out, s);
   return rc < 0 ? BOYS_ERR_NMAX : rc;
 }
 
@@ -301,7 +308,7 @@ boys_status boys_eval_contract_f64(const double *x, int64_t count, int n_max, co
 boys_status boys_eval_contract_f32(const float *x, int64_t count, int n_max, const float *c, int64_t c_row,
                                    int64_t c_col, float *out, void *stream) {
   if (count < 0) return BOYS_ERR_COUNT;
-  if (n_max < 0 || n_max > kMaxNF32) return BOYS_ERR_NMAX;
+  if (n_max < 0 || n_max > kMaxNF32Contract) return BOYS_ERR_NMAX;
   if (c_row < 0 || c_col < 0) return BOYS_ERR_ARG;
   if (count == 0) return BOYS_OK;
   if (!x || !c || !out) return BOYS_ERR_NULL;

@@ -39,7 +39,9 @@ constexpr int kMaxNF64 = 36;
 // n_top for the float path: the closed form of order n_max itself up to 8,
 // one order higher above (Sec. 3's F_{n+1} trick) to keep F_{n_max} within 2e-6.
 __host__ __device__ constexpr int f32_top_order(int n_max) { return n_max <= 8 ? n_max : n_max + 1; }
-constexpr int kMaxNF32 = 16;
+constexpr int kMaxNF32 = 36;
+// the fused float contraction keeps plain FP32 Horner sums: up to n_max = 16
+constexpr int kMaxNF32Contract = 16;
 
 // Persistent-grid size for a kernel: resident blocks per SM times SM count.
 template <typename Kernel>

@@ -37,9 +37,12 @@ struct F32Tile {
   static constexpr int WO = MODE == 0 ? W : 1;  // floats written per argument
   // 8 arguments per thread; small blocks keep the closed-form list's last
   // round of a tile well filled (about 30% of a tile is listed, and a block
-  // waits for its slowest warp), measured best on GB300 for each band
-  static constexpr int TILE = TILE_ ? TILE_ : (W <= 9 || MODE == 1 ? 1024 : 512);
-  static constexpr int BLOCK = BLOCK_ ? BLOCK_ : (W <= 9 || MODE == 1 ? 128 : 64);
+  // waits for its slowest warp), measured best on GB300 for each band.
+  // Above n_max = 16 a row is up to 148 bytes: 2 arguments per thread in
+  // 128-thread blocks (2^24 arguments: n_max = 36 at 1347 G values/s, against
+  // 1079 with 64/256, 1271 with 64/128, 1237 with 128/128, 897 with 128/512)
+  static constexpr int TILE = TILE_ ? TILE_ : (W <= 9 || MODE == 1 ? 1024 : W <= 17 ? 512 : 256);
+  static constexpr int BLOCK = BLOCK_ ? BLOCK_ : (W <= 9 || MODE == 1 ? 128 : W <= 17 ? 64 : 128);
   // rows[TILE*WO] floats, xs[TILE] floats, tab[64] floats, lst[TILE] u16
   static constexpr size_t kSmem = sizeof(float) * (TILE + TILE * WO + 64) + sizeof(unsigned short) * TILE;
 };

@@ -123,46 +123,122 @@ BOYS_F32_DEVFN float f32_power_tail(ff a) {
 
 // Below the cut-off z_{NTOP,24}: Eqs. "pqz", "fq" and "r" (denominator read
 // as 2m-1), as in the double path.
+// 1/d as a pair of floats, h + l, for the long recursions
+template <int D>
+struct F32RecipPair {
+  static constexpr float h = 1.0f / float(D);
+  static constexpr float l = float(1.0 / double(D) - double(h));
+};
+
+// Eq. "r" from F_M (in fm) down to F_0, storing F_m for m <= NMAX, with
+// 1/(2m - 1) as a float pair: over a long recursion the rounding of the
+// constants themselves, the same for every argument, would otherwise add up.
+template <int M, int NMAX>
+BOYS_F32_DEVFN void f32_recurse_pair(const float tx, const float e, float &fm, float (&F)[NMAX + 1]) {
+  if constexpr (M <= NMAX) F[M] = fm;
+  if constexpr (M >= 1) {
+    const float sm = fmaf(tx, fm, e);
+    fm = fmaf(sm, F32RecipPair<2 * M - 1>::h, sm * F32RecipPair<2 * M - 1>::l);
+    f32_recurse_pair<M - 1, NMAX>(tx, e, fm, F);
+  }
+}
+
+// From this order on the float path evaluates the rational part of Q~ in
+// float-float: the closed form multiplies a relative error of Q by s^2 (T/D),
+// and at high orders T/D stays near 1 far out in x, where q2 x^2 u/v is a
+// large part of Q (at n = 37, float u/v and float coefficients cost the
+// closed form 5e-6; in float-float it keeps about 1e-6).
+constexpr int kF32FFRationalFrom = 18;
+
 template <int NTOP, int NMAX>
 BOYS_F32_DEVFN void f32_formula(const float x, float (&F)[NMAX + 1], const float *tab) {
   using Tab = BoysF32<NTOP>;
-  float u, v;
-  Tab::uv(x, u, v);
-  // the rational part enters Q with weight ~x^2, where the amplification has
-  // fallen off: a couple of ulp in u/v cost nothing measurable
-  const float t = ((Tab::kQ2 * x) * x) * boys_fdiv_approx(u, v);
   ff q = ff_add(ff{Tab::kQ0hi, Tab::kQ0lo}, ff_mul_f(ff{Tab::kQ1hi, Tab::kQ1lo}, x));
-  q = ff_add_f(q, t);
+  if constexpr (NTOP < kF32FFRationalFrom) {
+    float u, v;
+    Tab::uv(x, u, v);
+    // the rational part enters Q with weight ~x^2, where the amplification has
+    // fallen off: a couple of ulp in u/v cost nothing measurable
+    const float t = ((Tab::kQ2 * x) * x) * boys_fdiv_approx(u, v);
+    q = ff_add_f(q, t);
+  } else {
+    ff u, v;
+    Tab::uv_ff(x, u, v);
+    const ff r = ff_mul(u, ff_rcp(v, boys_fdiv_approx(1.0f, v.hi)));
+    q = ff_add(q, ff_mul(ff_mul_f(ff_mul_f(ff{Tab::kQ2, Tab::kQ2lo}, x), x), r));
+  }
   const ff e = ff_exp_neg(x, tab);
   const ff T = ff_mul(ff_mul(ff_ipow<NTOP>(q), ff_sqrt(q, boys_rsqrtf(q.hi))), e);
   const ff D = ff_add_f(T, x);
   const ff w = ff_rcp(D, boys_fdiv_approx(1.0f, D.hi));  // seed; the Newton step restores ~46 bits
   // D^{-s} = w^NTOP sqrt(w): w carries the error of D amplified by s, so it
   // stays float-float; the power is float-float up to its last squaring,
-  // which (with sqrt(w) and c) rounds only a few times in FP32
-  const float f = f32_power_tail<NTOP>(w) * (Tab::kChi * (w.hi * boys_rsqrtf(w.hi)));
+  // which (with sqrt(w) and c) rounds only a few times in FP32.  Above
+  // n = 17, c_n and w^NTOP would leave the float range (c_35 > FLT_MAX, and
+  // w^NTOP < FLT_MIN near the cut-off) although F_n does not, so there
+  // F_n = (C w)^NTOP sqrt(C w) with C = c_n^(1/(n+1/2)), about 13 at n = 37.
+  float f;
+  if constexpr (NTOP <= 17) {
+    f = f32_power_tail<NTOP>(w) * (Tab::kChi * (w.hi * boys_rsqrtf(w.hi)));
+  } else {
+    const ff cw = ff_mul(ff{Tab::kCshi, Tab::kCslo}, w);
+    f = f32_power_tail<NTOP>(cw) * (cw.hi * boys_rsqrtf(cw.hi));
+  }
   const float tx = x + x;
   float fm = f;
+  if constexpr (NTOP < kF32FFRationalFrom) {
 #pragma unroll
-  for (int m = NTOP; m >= 1; --m) {
-    if (m <= NMAX) F[m] = fm;
-    fm = fmaf(tx, fm, e.hi) * (1.0f / float(2 * m - 1));
+    for (int m = NTOP; m >= 1; --m) {
+      if (m <= NMAX) F[m] = fm;
+      fm = fmaf(tx, fm, e.hi) * (1.0f / float(2 * m - 1));
+    }
+    F[0] = fm;
+  } else {
+    f32_recurse_pair<NTOP, NMAX>(tx, e.hi, fm, F);
   }
-  F[0] = fm;
 }
 
+// From this n_max on the asymptote's chain is compensated (below).
+constexpr int kF32CompensatedChainFrom = 17;
+
 // Above the cut-off (or x negative, infinite or NaN): the asymptote of
-// Eq. "limf1" built upward from F_0 = c_0 / sqrt(x).
+// Eq. "limf1" built upward from F_0 = c_0 / sqrt(x),
+// F_m = F_{m-1} (m - 1/2) y with y = 1/x.
+// In plain FP32 each order adds two roundings, and the rounding of y itself
+// grows as m in y^m: about 2.5e-6 at m = 36.  From n_max = 17 on the chain
+// is a compensated product (Graillat, IEEE Trans. Comput. 58(7), 2009): the
+// exact rounding errors of a_m = (m - 1/2) y and of each product, found with
+// fused multiply-adds, are carried in e and added back to every F_m, and the
+// error of y is removed through rho = 1 - x y (1/x = y (1 + rho + ...), so
+// y^m carries a factor 1 + m rho).  Every F_m is then within about one
+// rounding of c_0 x^{-1/2} prod (k - 1/2) / x.
 template <int NMAX>
 BOYS_F32_DEVFN void f32_asymptote(const float x, float (&F)[NMAX + 1]) {
   const float rs = boys_rsqrtf(x);
   float f = 0.886226925452758f * rs;
   F[0] = f;
   const float y = boys_frcp_rn(x);
+  if constexpr (NMAX < kF32CompensatedChainFrom) {
 #pragma unroll
-  for (int m = 1; m <= NMAX; ++m) {
-    f = f * ((float(m) - 0.5f) * y);
-    F[m] = f;
+    for (int m = 1; m <= NMAX; ++m) {
+      f = f * ((float(m) - 0.5f) * y);
+      F[m] = f;
+    }
+  } else {
+    // x = +inf gives y = 0 and the row 0; rho would be NaN there
+    const float rho = x < 3.0e38f ? fmaf(-x, y, 1.0f) : 0.0f;
+    float e = 0.0f;
+#pragma unroll
+    for (int m = 1; m <= NMAX; ++m) {
+      const float h = float(m) - 0.5f;
+      const float a = h * y;
+      const float ea = fmaf(h, y, -a);  // exact: a + ea = h y
+      const float p = f * a;
+      const float ep = fmaf(f, a, -p);  // exact: p + ep = f a
+      e = fmaf(e, a, fmaf(f, ea, ep));
+      f = p;
+      F[m] = fmaf(f, float(m) * rho, f + e);
+    }
   }
 }
 

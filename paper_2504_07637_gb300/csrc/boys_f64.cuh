@@ -711,122 +711,147 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
     x = sm.xs[j];
     return j;
   };
-  for (;;) {
-    int c = 0;
-    if (lane == 0) c = atomicAdd(&sm.next[0], CHUNK);
-    c = __shfl_sync(0xffffffffu, c, 0);
-    if (c >= flo) break;
-    const int q = c + lane;
-    if constexpr (STAGED) {
-      // the whole warp takes part; lanes past the end of the list compute a
-      // dummy argument and store nothing (with 32 entries or fewer left, one
-      // entry per lane)
-      if constexpr (ILP == 2) {
-        if (flo - c <= 32) {
-          double x1[1] = {1.0};
-          int j1[1] = {kNoRow};
-          if (q < flo) j1[0] = entry(0, q, x1[0]);
-          f64_formula_staged<NTOP, NMAX, STAGE, 1, TWO>(x1, j1, epi.out, stg, sm.tab64, lane);
-          continue;
-        }
-      }
-      int j[ILP];
-      double xv[ILP];
-#pragma unroll
-      for (int k = 0; k < ILP; ++k) {
-        xv[k] = 1.0;
-        j[k] = kNoRow;
-        if (q + 32 * k < flo) j[k] = entry(0, q + 32 * k, xv[k]);
-      }
-      f64_formula_staged<NTOP, NMAX, STAGE, ILP, TWO>(xv, j, epi.out, stg, sm.tab64, lane);
-      continue;
-    }
-    if constexpr (ILP == 2) {
-      if (q + 32 < flo) {
-        double xa, xb;
-        const int ja = entry(0, q, xa), jb = entry(0, q + 32, xb);
-        double Fa[W], Fb[W];
-        f64_formula<NTOP, NMAX>(xa, Fa, sm.tab64);
-        f64_formula<NTOP, NMAX>(xb, Fb, sm.tab64);
-        epi(ja, Fa);
-        epi(jb, Fb);
-        continue;
-      }
-    }
-    if (q < flo) {
-      double xq;
-      const int j = entry(0, q, xq);
-      double F[W];
-      if constexpr (TWO) {
-        constexpr int NBAR = f64_two_point_nbar(NMAX);
-        f64_formula_two<NTOP, f64_top_order(NBAR), NBAR, NMAX>(xq, F, sm.tab64);
-      } else {
-        f64_formula<NTOP, NMAX>(xq, F, sm.tab64);
-      }
-      epi(j, F);
-    }
-  }
-  // asymptote on the above-cut-off list (two entries per lane for high
-  // orders, as above: the upward product chain is 2 n_max long)
-  for (;;) {
-    int c = 0;
-    if (lane == 0) c = atomicAdd(&sm.next[1], CHUNK);
-    c = __shfl_sync(0xffffffffu, c, 0);
-    if (c >= fhi) break;
-    const int q = c + lane;
-    if constexpr (Epi::kHorner) {
-      if (epi.uniform()) {  // the contraction of the asymptote as a polynomial
-#pragma unroll
-        for (int k = 0; k < ILP; ++k) {
-          if (q + 32 * k < fhi) {
-            double xq;
-            const int j = entry(1, q + 32 * k, xq);
-            epi.put(j, epi.asymptote_dot(xq));
+  auto below_loop = [&]() {
+    for (;;) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(&sm.next[0], CHUNK);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      if (c >= flo) break;
+      const int q = c + lane;
+      if constexpr (STAGED) {
+        // the whole warp takes part; lanes past the end of the list compute a
+        // dummy argument and store nothing (with 32 entries or fewer left, one
+        // entry per lane)
+        if constexpr (ILP == 2) {
+          if (flo - c <= 32) {
+            double x1[1] = {1.0};
+            int j1[1] = {kNoRow};
+            if (q < flo) j1[0] = entry(0, q, x1[0]);
+            f64_formula_staged<NTOP, NMAX, STAGE, 1, TWO>(x1, j1, epi.out, stg, sm.tab64, lane);
+            continue;
           }
         }
+        int j[ILP];
+        double xv[ILP];
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) {
+          xv[k] = 1.0;
+          j[k] = kNoRow;
+          if (q + 32 * k < flo) j[k] = entry(0, q + 32 * k, xv[k]);
+        }
+        f64_formula_staged<NTOP, NMAX, STAGE, ILP, TWO>(xv, j, epi.out, stg, sm.tab64, lane);
         continue;
       }
-    }
-    if constexpr (STAGED) {
       if constexpr (ILP == 2) {
-        if (fhi - c <= 32) {
-          double x1[1] = {1.0};
-          int j1[1] = {kNoRow};
-          if (q < fhi) j1[0] = entry(1, q, x1[0]);
-          f64_asymptote_staged<NMAX, STAGE, 1>(x1, j1, epi.out, stg, lane);
+        if (q + 32 < flo) {
+          double xa, xb;
+          const int ja = entry(0, q, xa), jb = entry(0, q + 32, xb);
+          double Fa[W], Fb[W];
+          f64_formula<NTOP, NMAX>(xa, Fa, sm.tab64);
+          f64_formula<NTOP, NMAX>(xb, Fb, sm.tab64);
+          epi(ja, Fa);
+          epi(jb, Fb);
           continue;
         }
       }
-      int j[ILP];
-      double xv[ILP];
-#pragma unroll
-      for (int k = 0; k < ILP; ++k) {
-        xv[k] = 1.0;
-        j[k] = kNoRow;
-        if (q + 32 * k < fhi) j[k] = entry(1, q + 32 * k, xv[k]);
+      if (q < flo) {
+        double xq;
+        const int j = entry(0, q, xq);
+        double F[W];
+        if constexpr (TWO) {
+          constexpr int NBAR = f64_two_point_nbar(NMAX);
+          f64_formula_two<NTOP, f64_top_order(NBAR), NBAR, NMAX>(xq, F, sm.tab64);
+        } else {
+          f64_formula<NTOP, NMAX>(xq, F, sm.tab64);
+        }
+        epi(j, F);
       }
-      f64_asymptote_staged<NMAX, STAGE, ILP>(xv, j, epi.out, stg, lane);
-      continue;
     }
-    if constexpr (ILP == 2) {
-      if (q + 32 < fhi) {
-        double xa, xb;
-        const int ja = entry(1, q, xa), jb = entry(1, q + 32, xb);
-        double Fa[W], Fb[W];
-        f64_asymptote<NMAX>(xa, Fa);
-        f64_asymptote<NMAX>(xb, Fb);
-        epi(ja, Fa);
-        epi(jb, Fb);
+  };
+  auto above_loop = [&]() {
+    // asymptote on the above-cut-off list (two entries per lane for high
+    // orders, as above: the upward product chain is 2 n_max long)
+    for (;;) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(&sm.next[1], CHUNK);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      if (c >= fhi) break;
+      const int q = c + lane;
+      if constexpr (Epi::kHorner) {
+        if (epi.uniform()) {  // the contraction of the asymptote as a polynomial
+#pragma unroll
+          for (int k = 0; k < ILP; ++k) {
+            if (q + 32 * k < fhi) {
+              double xq;
+              const int j = entry(1, q + 32 * k, xq);
+              epi.put(j, epi.asymptote_dot(xq));
+            }
+          }
+          continue;
+        }
+      }
+      if constexpr (STAGED) {
+        if constexpr (ILP == 2) {
+          if (fhi - c <= 32) {
+            double x1[1] = {1.0};
+            int j1[1] = {kNoRow};
+            if (q < fhi) j1[0] = entry(1, q, x1[0]);
+            f64_asymptote_staged<NMAX, STAGE, 1>(x1, j1, epi.out, stg, lane);
+            continue;
+          }
+        }
+        int j[ILP];
+        double xv[ILP];
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) {
+          xv[k] = 1.0;
+          j[k] = kNoRow;
+          if (q + 32 * k < fhi) j[k] = entry(1, q + 32 * k, xv[k]);
+        }
+        f64_asymptote_staged<NMAX, STAGE, ILP>(xv, j, epi.out, stg, lane);
         continue;
       }
+      if constexpr (ILP == 2) {
+        if (q + 32 < fhi) {
+          double xa, xb;
+          const int ja = entry(1, q, xa), jb = entry(1, q + 32, xb);
+          double Fa[W], Fb[W];
+          f64_asymptote<NMAX>(xa, Fa);
+          f64_asymptote<NMAX>(xb, Fb);
+          epi(ja, Fa);
+          epi(jb, Fb);
+          continue;
+        }
+      }
+      if (q < fhi) {
+        double xq;
+        const int j = entry(1, q, xq);
+        double F[W];
+        f64_asymptote<NMAX>(xq, F);
+        epi(j, F);
+      }
     }
-    if (q < fhi) {
-      double xq;
-      const int j = entry(1, q, xq);
-      double F[W];
-      f64_asymptote<NMAX>(xq, F);
-      epi(j, F);
+  };
+  // Even warps start on the closed-form list, odd warps on the asymptote
+  // list, and each then helps with the other one, so FP64-bound and
+  // integer-bound requests run side by side instead of one list after
+  // the other (n_max = 8: 139.5 -> 142.9 G values/s; two-point n_max = 36:
+  // 163.9 -> 171.5).  The staged one-point rows keep the plain order: there
+  // the two live phases cost registers and spills (n_max = 36: 200 -> 181).
+  constexpr bool MIX = !STAGED || TWO;
+  if constexpr (MIX) {
+    const int par = (threadIdx.x >> 5) & 1;
+#pragma unroll 1
+    for (int ph = 0; ph < 2; ++ph) {
+      if ((ph ^ par) == 0) {
+        below_loop();
+      } else {
+        above_loop();
+      }
     }
+  } else {
+    below_loop();
+    above_loop();
   }
   __syncthreads();
   if constexpr (CARRY) {

@@ -79,6 +79,13 @@ BOYS_FF_HD ff ff_add_f(ff a, float b) {
   return fast_two_sum(s.hi, s.lo + a.lo);
 }
 
+// x - y for any signs (the root factors x - y of Eqs. "pz"/"qz"): Knuth's
+// error-free sum of x and -y.hi, then y.lo
+BOYS_FF_HD ff ff_sub_f(ff y, float x) {
+  const ff s = two_sum(x, -y.hi);
+  return fast_two_sum(s.hi, s.lo - y.lo);
+}
+
 // sqrt(a), a > 0: seed s = a.hi * rsqrt(a.hi), then one correction with the
 // exact residual a - s^2 (Karp and Markstein, ACM TOMS 23(4), 1997)
 BOYS_FF_HD ff ff_sqrt(ff a, float rs) {

@@ -151,6 +151,45 @@ def f_split(v: str) -> tuple[str, str]:
     return fmt(hi), fmt(lo)
 
 
+def ff_lit(v: str) -> str:
+    """Decimal string -> ff{hi, lo} literal (float-float, about 48 bits)."""
+    hi, lo = f_split(v)
+    return f"ff{{{hi}, {lo}}}"
+
+
+def poly_lines_ff(name: str, fac: dict) -> list[str]:
+    """Statements computing the monic root-product polynomial into the
+    float-float `name`, with float-float coefficients: the same factors as
+    poly_lines, for the orders whose rounding is amplified beyond float."""
+    poly = fac["poly"]
+    lines = [f"ff {name};"]
+    state = {"first": True}
+
+    def mul(expr: str, indent: str = "") -> None:
+        if state["first"]:
+            lines.append(f"{indent}{name} = {expr};")
+            state["first"] = False
+        else:
+            lines.append(f"{indent}{name} = ff_mul({name}, {expr});")
+
+    if len(poly) > 1:
+        # the gathered negative-real-part roots: positive coefficients
+        lines.append(f"{{ ff h = ff_add_f({ff_lit(poly[-2])}, x);")
+        for c in reversed(poly[:-2]):
+            lines.append(f"  h = ff_add(ff_mul_f(h, x), {ff_lit(c)});")
+        mul("h", "  ")
+        lines.append("}")
+    for y, a in fac["quad"]:
+        lines.append(f"{{ const ff t = ff_sub_f({ff_lit(y)}, x);")  # x - y
+        mul(f"ff_add(ff_sqr(t), {ff_lit(a)})", "  ")
+        lines.append("}")
+    for y in fac["lin"]:
+        mul(f"ff_sub_f({ff_lit(y)}, x)")
+    if state["first"]:
+        lines.append(f"{name} = ff{{1.0f, 0.0f}};")
+    return lines
+
+
 def emit_f32(table: dict, source: str) -> str:
     fits = {r["n"]: r for r in table["fits"]}
     nmax = max(fits)
@@ -169,10 +208,15 @@ def emit_f32(table: dict, source: str) -> str:
         r = fits[n]
         q0 = f_split(r["q0"])
         q1 = f_split(r["q1"])
-        c = f_split(r["c"])
+        # c_n leaves the float range from n = 35 on; the kernels of high
+        # orders use C = c_n^(1/(n+1/2)) instead, F_n = (C / D)^(n+1/2)
+        c = f_split(r["c"]) if float(r["c"]) < 3.0e38 else ("0.0f", "0.0f")
+        cs = f_split(c_root(r["c"], n))
         host_z.append(f(r["z"]))
         body = ["    " + ln for ln in poly_lines("u", r["u"], fma="fmaf", ty="float", lit=f)]
         body += ["    " + ln for ln in poly_lines("v", r["v"], fma="fmaf", ty="float", lit=f)]
+        body_ff = ["    " + ln for ln in poly_lines_ff("u", r["u"])]
+        body_ff += ["    " + ln for ln in poly_lines_ff("v", r["v"])]
         out += [
             f"// n = {n}: N = {r['N']}, exact-arithmetic error 2^-{r['eps_bits']:.2f}",
             f"template <> struct BoysF32<{n}> {{",
@@ -181,9 +225,18 @@ def emit_f32(table: dict, source: str) -> str:
             f"  static constexpr float kQ0hi = {q0[0]}, kQ0lo = {q0[1]};",
             f"  static constexpr float kQ1hi = {q1[0]}, kQ1lo = {q1[1]};",
             f"  static constexpr float kQ2 = {f(r['q2'])};",
-            f"  static constexpr float kChi = {c[0]}, kClo = {c[1]};",
+            f"  static constexpr float kChi = {c[0]}, kClo = {c[1]};" + ("" if c[0] != "0.0f" else "  // beyond the float range"),
+            f"  static constexpr float kCshi = {cs[0]}, kCslo = {cs[1]};  // c_n^(1/(n+1/2))",
+            f"  static constexpr float kQ2lo = {f_split(r['q2'])[1]};  // q2 = kQ2 + kQ2lo",
             "  static BOYS_FF_HD void uv(float x, float &u_out, float &v_out) {",
             *body,
+            "    u_out = u;",
+            "    v_out = v;",
+            "  }",
+            "  // the same in float-float, coefficients to about 48 bits",
+            "  static BOYS_FF_HD void uv_ff(float x, boys::ff &u_out, boys::ff &v_out) {",
+            "    using namespace boys;",
+            *body_ff,
             "    u_out = u;",
             "    v_out = v;",
             "  }",
@@ -192,6 +245,14 @@ def emit_f32(table: dict, source: str) -> str:
         ]
     out += [f"static const float kBoysF32CutoffHost[{nmax + 1}] = {{" + ", ".join(host_z) + "};", ""]
     return "\n".join(out)
+
+
+def c_root(c: str, n: int) -> str:
+    """c^(1/(n+1/2)) as a 40-digit decimal string."""
+    import mpmath as mp
+
+    mp.mp.dps = 50
+    return mp.nstr(mp.mpf(c) ** (1 / (mp.mpf(n) + mp.mpf(1) / 2)), 40)
 
 
 def exp2_table_ff(n: int = 32) -> str:

@@ -34,8 +34,14 @@ def _table1():
 
 
 def _fits(bits):
+    """A fitted table: 53 and 24 are Table I's orders; "24_plus1" is the float
+    path's table, one order N above the single-precision column."""
     with open(os.path.join(COEFFS, f"boys_fit_b{bits}.json")) as fh:
         return {r["n"]: r for r in json.load(fh)["fits"]}
+
+
+def _bits(table):
+    return 53 if table == 53 else 24
 
 
 def _factors(d, conv):
@@ -76,7 +82,17 @@ def test_orders_and_accuracy_match_table1(bits):
         assert abs(rec["eps_bits"] - t1[n][f"eps{bits}"]) <= 0.1, (n, rec["eps_bits"], t1[n][f"eps{bits}"])
 
 
-@pytest.mark.parametrize("bits,n", [(53, n) for n in (0, 4, 8, 9, 17, 37)] + [(24, n) for n in (0, 5, 8, 9, 20)])
+def test_float_path_table_is_one_order_above_table1():
+    # the float kernels evaluate up to n_top = 37 with fits of order N + 1
+    t1, fits = _table1(), _fits("24_plus1")
+    assert set(range(38)) <= set(fits)
+    for n, rec in fits.items():
+        assert rec["N"] == (t1[min(n, 36)]["N24"] + 1), n
+        assert rec["eps_bits"] >= 23.5, (n, rec["eps_bits"])
+
+
+@pytest.mark.parametrize("bits,n", [(53, n) for n in (0, 4, 8, 9, 17, 37)] + [(24, n) for n in (0, 5, 8, 9, 20)]
+                         + [("24_plus1", n) for n in (0, 9, 21, 30, 37)])
 def test_approximation_against_oracle(oracle_mod, bits, n):
     mp.mp.dps = 40
     rec = _fits(bits)[n]
@@ -102,7 +118,7 @@ def test_approximation_against_oracle(oracle_mod, bits, n):
         assert worst_rounded <= 1.25 * e_fit + max(1.0, 2 * s2) * 2.0**-52 + e_oracle, (worst_rounded, e_fit)
 
 
-@pytest.mark.parametrize("bits", [53, 24])
+@pytest.mark.parametrize("bits", [53, 24, "24_plus1"])
 def test_built_in_constraints(oracle_mod, bits):
     mp.mp.dps = 50
     for n, rec in sorted(_fits(bits).items()):
@@ -126,7 +142,7 @@ def test_built_in_constraints(oracle_mod, bits):
         assert abs(mp.mpf(rec["beta"]) - mp.mpf(2 * n - 1) / (2 * n + 1) * mp.mpf(rec["alpha"])) < 1e-30
 
 
-@pytest.mark.parametrize("bits", [53, 24])
+@pytest.mark.parametrize("bits", [53, 24, "24_plus1"])
 def test_no_pole_on_positive_axis(bits):
     mp.mp.dps = 40
     for n, rec in _fits(bits).items():
@@ -138,10 +154,10 @@ def test_no_pole_on_positive_axis(bits):
             assert mp.mpf(a) > 0, n
 
 
-@pytest.mark.parametrize("bits", [53, 24])
+@pytest.mark.parametrize("bits", [53, 24, "24_plus1"])
 def test_cutoffs_match_oracle(oracle_mod, bits):
     for n, rec in _fits(bits).items():
-        assert abs(float(mp.mpf(rec["z"])) / oracle_mod.cutoff(n, bits) - 1) < 1e-14
+        assert abs(float(mp.mpf(rec["z"])) / oracle_mod.cutoff(n, _bits(bits)) - 1) < 1e-14
 
 
 def _roots(fac):

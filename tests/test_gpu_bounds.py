@@ -79,7 +79,7 @@ def test_rows_f64_two_point(env, n_max, count):
     _check(torch, buf, n)
 
 
-@pytest.mark.parametrize("n_max", [0, 8, 9, 16])
+@pytest.mark.parametrize("n_max", [0, 8, 9, 16, 17, 36])
 @pytest.mark.parametrize("count", [1, 33, 1025, 4097, (1 << 22) + 5])
 def test_rows_f32(env, n_max, count):
     torch, capi, workloads = env

@@ -82,7 +82,7 @@ def test_plain_workload_n8(lib, oracle_mod, record_property):
     assert per_m.max() <= TOL, per_m
 
 
-@pytest.mark.parametrize("n_max", list(range(0, 17)))
+@pytest.mark.parametrize("n_max", list(range(0, 37)))
 def test_every_order(lib, oracle_mod, n_max, record_property):
     rng = np.random.default_rng(300 + n_max)
     z = lib.cutoff(lib.top_order_f32(n_max), 24)
@@ -103,15 +103,15 @@ def test_every_order(lib, oracle_mod, n_max, record_property):
 
 
 def test_special_arguments(lib, oracle_mod):
-    zs = [np.float32(lib.cutoff(n, 24)) for n in range(0, 18)]
+    zs = [np.float32(lib.cutoff(n, 24)) for n in range(0, 38)]
     near = [np.nextafter(z, np.float32(0)) for z in zs] + zs + [np.nextafter(z, np.float32(np.inf)) for z in zs]
     x = np.array([0.0, -0.0, 1e-45, 1e-40, 1.1754944e-38, 1e-30, 1e-7, 1.0, 1e6, 1e20, 3.4e38] + near,
                  dtype=np.float32)
-    for n_max in (0, 8, 16):
+    for n_max in (0, 8, 16, 17, 24, 36):
         got, xf = _gpu(lib, x, n_max)
         rel = _check(got, oracle_mod.boys(xf.astype(np.float64), n_max))
         assert rel.max() <= TOL, (n_max, xf[np.argmax(rel.max(axis=1))])
-    for n_max in (8, 16):  # both tile shapes
+    for n_max in (8, 16, 17, 36):  # every tile shape, and the compensated chain
         bad, _ = _gpu(lib, np.array([-1.0, -1e-30, np.nan, -np.inf, np.inf], dtype=np.float32), n_max)
         assert np.all(np.isnan(bad[:4])) and np.all(bad[4] == 0.0)
 
@@ -158,6 +158,39 @@ def test_full_size_scale_workload_sampled(lib, oracle_mod, record_property):
     assert rel.max() <= TOL
     del out
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n_max", [24, 36])
+def test_full_size_high_order_sampled(lib, oracle_mod, n_max, record_property):
+    # 2^24 float arguments of the scale workload at the high orders (float-float
+    # rational part, paired recursion constants, compensated asymptote chain)
+    import torch
+
+    from paper_2504_07637_gb300 import workloads
+
+    xf = workloads.scale(1 << 24, seed=36).astype(np.float32)
+    out = lib.boys(torch.from_numpy(xf).cuda(), n_max)
+    idx = np.sort(np.random.default_rng(n_max).choice(xf.size, 1 << 18, replace=False))
+    idx = np.concatenate([idx, [0, xf.size - 1]])
+    got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
+    rel = _check(got, oracle_mod.boys_threaded(xf[idx].astype(np.float64), n_max, os.cpu_count() or 1))
+    record_property("max_rel_err_per_m", _per_m(rel))
+    assert rel.max() <= TOL
+    del out
+    torch.cuda.empty_cache()
+
+
+def test_contraction_order_limit(lib):
+    # the fused float contraction stays at n_max <= 16 (plain FP32 Horner sums)
+    import torch
+
+    from paper_2504_07637_gb300 import _capi
+
+    x = torch.ones(4, dtype=torch.float32, device="cuda")
+    c = torch.ones(18, dtype=torch.float32, device="cuda")
+    out = torch.empty(4, dtype=torch.float32, device="cuda")
+    rc = _capi.load().boys_eval_contract_f32(x.data_ptr(), 4, 17, c.data_ptr(), 0, 1, out.data_ptr(), None)
+    assert rc == 3  # BOYS_ERR_NMAX
 
 
 def test_host_pipeline_matches_device_path(lib):
