@@ -19,11 +19,12 @@
 //    |r| <= ln2/128, about 10 FP64 operations.
 //  * Half-integer powers use the reciprocal square root where the rounding
 //    budget allows it.
-//  * From n_max = 12 on, a lane takes two list entries (two independent
-//    recursion chains), and the rows of a store leave through a per-warp
-//    shared-memory staging buffer in row order.  Rows stored straight from
-//    registers touch 32 sectors per warp instruction, and those stores back
-//    up into the FP64 instruction stream.
+//  * From n_max = 12 on, the rows leave through a per-warp shared-memory
+//    staging buffer, 16 orders of 32 rows at a time (two-point rows: 8
+//    orders of 64 rows, two list entries per lane), in row order.  Rows
+//    stored straight from registers touch 32 sectors per warp instruction,
+//    and those stores back up into the instruction stream; at n_max = 36 the
+//    stores, not the arithmetic, set the pace.
 #pragma once
 
 #include "boys_coeffs_f64.inc"
@@ -320,7 +321,7 @@ __device__ __forceinline__ void f64_asymptote(const double x, double (&F)[NMAX +
 // doubles apart).  Instead it collects F_m for CH consecutive m of its rows in
 // shared memory (odd row pitch: conflict-free 64-bit lane access) and writes
 // each 32K x LEN block with consecutive lanes on consecutive elements of a
-// row, about 11 sectors per store at CH = 8.
+// row: a store instruction covers 32 / LEN row segments of LEN doubles.
 template <int CH, int K>
 struct F64Stage {
   static constexpr int kPitch = CH | 1;
@@ -501,14 +502,32 @@ __device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const
     static_for<(CF + 1 > 1 ? CF + 1 : 1) * CH, W, 1>(unrolled);
     return;
   }
-  static_for<0, W, 1>([&](auto mc) {
+  // beyond the integer chain's range (x > 2^27 at n_max = 36; none of the
+  // benchmark arguments): the FP64 chain, looped over whole chunks to keep
+  // the code small
+  constexpr int CF = W / CH - 1;  // highest whole chunk (-1 if none)
+#pragma unroll 1
+  for (int c = 0; c <= CF; ++c) {
+    const int m0 = c * CH;
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      const int m = m0 + i;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (m > 0) f[k] = f[k] * ((double(m) - 0.5) * y[k]);
+        stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + i] = f[k];
+      }
+    }
+    f64_stage_flush<W, CH, K, CH>(out, stg, m0, j, lane);
+  }
+  static_for<(CF + 1) * CH, W, 1>([&](auto mc) {
     constexpr int m = decltype(mc)::value;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if constexpr (m > 0) f[k] = f[k] * ((double(m) - 0.5) * y[k]);
       stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + m % CH] = f[k];
     }
-    if constexpr (m % CH == CH - 1 || m == NMAX) f64_stage_flush<W, CH, K, m % CH + 1>(out, stg, m - m % CH, j, lane);
+    if constexpr (m == NMAX) f64_stage_flush<W, CH, K, m % CH + 1>(out, stg, m - m % CH, j, lane);
   });
 }
 
@@ -720,17 +739,10 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
       const int q = c + lane;
       if constexpr (STAGED) {
         // the whole warp takes part; lanes past the end of the list compute a
-        // dummy argument and store nothing (with 32 entries or fewer left, one
-        // entry per lane)
-        if constexpr (ILP == 2) {
-          if (flo - c <= 32) {
-            double x1[1] = {1.0};
-            int j1[1] = {kNoRow};
-            if (q < flo) j1[0] = entry(0, q, x1[0]);
-            f64_formula_staged<NTOP, NMAX, STAGE, 1, TWO>(x1, j1, epi.out, stg, sm.tab64, lane);
-            continue;
-          }
-        }
+        // dummy argument and store nothing.  (A one-entry-per-lane copy for
+        // the last request of a list saved that request's dummy work, but its
+        // code cost more in instruction fetch: 1.5-2% slower at n_max = 16
+        // and 36.)
         int j[ILP];
         double xv[ILP];
 #pragma unroll
@@ -791,15 +803,6 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
         }
       }
       if constexpr (STAGED) {
-        if constexpr (ILP == 2) {
-          if (fhi - c <= 32) {
-            double x1[1] = {1.0};
-            int j1[1] = {kNoRow};
-            if (q < fhi) j1[0] = entry(1, q, x1[0]);
-            f64_asymptote_staged<NMAX, STAGE, 1>(x1, j1, epi.out, stg, lane);
-            continue;
-          }
-        }
         int j[ILP];
         double xv[ILP];
 #pragma unroll
@@ -1027,13 +1030,22 @@ int launch_f64_epi(const double *x, int64_t count, const MakeEpi &epi, cudaStrea
   return launch_f64_shape<NMAX, kF64Block, kF64Tile, MakeEpi, TWO, STAGE, K>(x, count, epi, s);
 }
 
-// Orders staged per flush of the row-staging buffer (rows of n_max >= 12,
-// where lanes take two list entries).
-constexpr int kF64StageOrders = 8;
+// Row staging from n_max = 12 on: orders per flush of the staging buffer
+// and list entries per lane.  The one-point rows flush 16 orders of 32 rows
+// (each store instruction then covers two row segments of 128 bytes): with
+// the arithmetic stubbed out, n_max = 36 spent 2.6 ms of its 3.1 ms on the
+// stores of 8-order flushes of 64 rows (four 64-byte segments per store
+// instruction), 2.05 ms with 16 orders of 64 rows, 1.5 ms with 32 orders of
+// 32 rows.  In full: n_max = 36 202.5 -> 250.0 G values/s, n_max = 16
+// 172.6 -> 189.6 (16 orders and two entries per lane: 166.5 and 161.2, two
+// resident blocks; whole rows per flush: 224.3 and 182.6).  The two-point rows
+// keep 8 orders and two entries per lane.
+constexpr int kF64StageOrders = 16, kF64StageK = 1;
+constexpr int kF64TwoStageOrders = 8, kF64TwoStageK = 2;
 
 template <int NMAX>
 int launch_f64(const double *x, int64_t count, double *out, cudaStream_t s) {
-  return launch_f64_epi<NMAX, MakeStore<NMAX + 1>, false, (NMAX >= 12 ? kF64StageOrders : 0)>(
+  return launch_f64_epi<NMAX, MakeStore<NMAX + 1>, false, (NMAX >= 12 ? kF64StageOrders : 0), kF64StageK>(
       x, count, MakeStore<NMAX + 1>{out}, s);
 }
 
@@ -1047,7 +1059,7 @@ int launch_f64_grad_recompute(const double *x, int64_t count, const double *g, i
 // Two-point evaluation (Trick B): rows as launch_f64.
 template <int NMAX>
 int launch_f64_two_point(const double *x, int64_t count, double *out, cudaStream_t s) {
-  return launch_f64_epi<NMAX, MakeStore<NMAX + 1>, true, (NMAX >= 12 ? kF64StageOrders : 0)>(
+  return launch_f64_epi<NMAX, MakeStore<NMAX + 1>, true, (NMAX >= 12 ? kF64TwoStageOrders : 0), kF64TwoStageK>(
       x, count, MakeStore<NMAX + 1>{out}, s);
 }
 
