@@ -20,8 +20,7 @@
 //  * Half-integer powers use the reciprocal square root where the rounding
 //    budget allows it.
 //  * From n_max = 12 on, the rows leave through a per-warp shared-memory
-//    staging buffer, 16 orders of 32 rows at a time (two-point rows: 8
-//    orders of 64 rows, two list entries per lane), in row order.  Rows
+//    staging buffer, 16 orders of 32 rows at a time, in row order.  Rows
 //    stored straight from registers touch 32 sectors per warp instruction,
 //    and those stores back up into the instruction stream; at n_max = 36 the
 //    stores, not the arithmetic, set the pace.
@@ -1039,9 +1038,9 @@ int launch_f64_epi(const double *x, int64_t count, const MakeEpi &epi, cudaStrea
 // 32 rows.  In full: n_max = 36 202.5 -> 250.0 G values/s, n_max = 16
 // 172.6 -> 189.6 (16 orders and two entries per lane: 166.5 and 161.2, two
 // resident blocks; whole rows per flush: 224.3 and 182.6).  The two-point rows
-// keep 8 orders and two entries per lane.
+// the same way: n_max = 36 173.7 -> 175.8.
 constexpr int kF64StageOrders = 16, kF64StageK = 1;
-constexpr int kF64TwoStageOrders = 8, kF64TwoStageK = 2;
+constexpr int kF64TwoStageOrders = 16, kF64TwoStageK = 1;
 
 template <int NMAX>
 int launch_f64(const double *x, int64_t count, double *out, cudaStream_t s) {
