@@ -44,6 +44,8 @@ WORKLOADS = {
     # differentiation: 2^24 arguments, forward to n_max = 9, backward of sum_{m<=8} w_m F_m
     "grad_f64": dict(count=1 << 24, n_max=8, dtype="f64", kind="grad"),
     # small cases of the same kernels for detailed profiling (outputs still larger than L2)
+    "scale_f64_n0_small": dict(count=1 << 22, n_max=0, dtype="f64"),
+    "scale_f64_n4_small": dict(count=1 << 22, n_max=4, dtype="f64"),
     "scale_f64_n8_small": dict(count=1 << 22, n_max=8, dtype="f64"),
     "scale_f32_n8_small": dict(count=1 << 24, n_max=8, dtype="f32"),
     "scale_f64_n16_small": dict(count=1 << 22, n_max=16, dtype="f64"),
@@ -606,6 +608,8 @@ def run_ragged(args, wl, emit=True):
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "note": "FP64-pipe instruction equivalents (per-request op-count model) vs the measured DFMA rate"},
     }
+    apply_ceiling(line["roofline"], pipe_ceiling("ragged<0..16>/plain", int(offsets[-1]), ms / 1e3, rates,
+                                                 ((clk or {}).get("sm_mhz") or SM_CLOCK_MAX_HZ / 1e6) * 1e6))
     if emit:
         print(json.dumps(line), flush=True)
     return line
@@ -1099,6 +1103,9 @@ def main():
         rg = run_ragged(sub, WORKLOADS["ragged_f64"], emit=False)
         suite["ragged_f64"] = {k: rg[k] for k in ("value", "unit", "ms_per_step", "latency_ms", "plain_launches")}
         suite["ragged_f64"]["roofline_frac"] = rg["roofline"]["frac"]
+        suite["ragged_f64"]["fp64_model_frac"] = rg["roofline"]["fp64_model"]["frac"]
+        c = rg["roofline"].get("ceiling")
+        suite["ragged_f64"]["ceiling_pipe"] = c["bound_pipe"] if c else None
         suite["ragged_f64"]["variant"] = rg["config"]["variant"]
         gr = run_grad(sub, WORKLOADS["grad_f64"], emit=False)
         suite["grad_f64"] = {k: gr[k] for k in ("value", "unit", "ms_per_step", "forward_ms", "backward_ms",

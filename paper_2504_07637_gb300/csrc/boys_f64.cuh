@@ -671,11 +671,8 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
     sm.next[0] = sm.next[1] = 0;
   }
   __syncthreads();
-#pragma unroll 4
-  for (int j0 = 0; j0 < TILE; j0 += BLOCK) {
-    const int j = j0 + threadIdx.x;
-    const bool valid = j < nel;
-    const double v = valid ? __ldcs(xt + j) : 0.0;
+  // argument j of the tile (value v) into its list
+  auto classify = [&](const int j, const double v, const bool valid) {
     sm.xs[j] = v;
     const bool lo = valid && below_cutoff(v, zbits);
     const bool hi = valid && !lo;
@@ -689,6 +686,57 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
     phi = __shfl_sync(0xffffffffu, phi, 0);
     if (lo) sm.lst[plo + __popc(mlo & lt)] = (unsigned short)j;
     if (hi) sm.lst[TILE - 1 - (phi + __popc(mhi & lt))] = (unsigned short)j;
+  };
+  // arguments j and j + 1 (values v.x, v.y) of a thread's pair into the
+  // lists, in argument order across the warp's 64 arguments (a list in
+  // argument order keeps the rows a warp request stores close together: with
+  // the even and the odd arguments listed apart, n_max = 8 fell from 143 to
+  // 105 G values/s)
+  auto classify2 = [&](const int j, const double2 v, const int nv) {
+    sm.xs[j] = v.x;
+    sm.xs[j + 1] = v.y;
+    const bool lo0 = nv > 0 && below_cutoff(v.x, zbits), hi0 = nv > 0 && !lo0;
+    const bool lo1 = nv > 1 && below_cutoff(v.y, zbits), hi1 = nv > 1 && !lo1;
+    const unsigned l0 = __ballot_sync(0xffffffffu, lo0), l1 = __ballot_sync(0xffffffffu, lo1);
+    const unsigned h0 = __ballot_sync(0xffffffffu, hi0), h1 = __ballot_sync(0xffffffffu, hi1);
+    int plo = 0, phi = 0;
+    if (lane == 0) {
+      if (l0 | l1) plo = atomicAdd(&sm.cnt[0], __popc(l0) + __popc(l1));
+      if (h0 | h1) phi = atomicAdd(&sm.cnt[1], __popc(h0) + __popc(h1));
+    }
+    plo = __shfl_sync(0xffffffffu, plo, 0) + __popc(l0 & lt) + __popc(l1 & lt);
+    phi = __shfl_sync(0xffffffffu, phi, 0) + __popc(h0 & lt) + __popc(h1 & lt);
+    if (lo0) sm.lst[plo] = (unsigned short)j;
+    if (lo1) sm.lst[plo + lo0] = (unsigned short)(j + 1);
+    if (hi0) sm.lst[TILE - 1 - phi] = (unsigned short)j;
+    if (hi1) sm.lst[TILE - 1 - (phi + hi0)] = (unsigned short)(j + 1);
+  };
+  bool scalar = true;
+  if constexpr (TILE % (2 * BLOCK) == 0) {
+    // 128-bit loads: two neighbouring arguments per thread where the tile
+    // starts on a 16-byte boundary (a plain evaluation's tiles do when x does)
+    if ((reinterpret_cast<uintptr_t>(xt) & 15) == 0) {
+      scalar = false;
+#pragma unroll 2
+      for (int p0 = 0; p0 < TILE / 2; p0 += BLOCK) {
+        const int j = 2 * (p0 + threadIdx.x);
+        double2 v = make_double2(0.0, 0.0);
+        if (j + 1 < nel) {
+          v = __ldcs(reinterpret_cast<const double2 *>(xt + j));
+        } else if (j < nel) {
+          v.x = __ldcs(xt + j);
+        }
+        classify2(j, v, nel - j);
+      }
+    }
+  }
+  if (scalar) {
+#pragma unroll 4
+    for (int j0 = 0; j0 < TILE; j0 += BLOCK) {
+      const int j = j0 + threadIdx.x;
+      const bool valid = j < nel;
+      classify(j, valid ? __ldcs(xt + j) : 0.0, valid);
+    }
   }
   __syncthreads();
   const int nlo = sm.cnt[0], nhi = sm.cnt[1];
