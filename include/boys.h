@@ -185,9 +185,10 @@ boys_status boys_eval_f64_host(const double *x_host, int64_t count, int n_max, d
  * request with a bad n_max, bad offsets or a range outside x_size/out_size
  * produces no values; it is counted (boys_ragged_errors) and, when its
  * output range lies inside [0, out_size), that range is filled with NaN.
- * The call enqueues one memset and two kernels (a one-block plan and the
- * persistent evaluation), allocates nothing and never synchronises, so it
- * can be captured in a CUDA graph and replayed. */
+ * The call enqueues one memset and two kernels (a one-block plan, which
+ * also orders the requests by n_max so that the GPU works on one order at a
+ * time, and the persistent evaluation), allocates nothing and never
+ * synchronises, so it can be captured in a CUDA graph and replayed. */
 size_t boys_ragged_workspace_bytes(int32_t num_requests);
 int boys_ragged_max_n(void);
 int boys_ragged_num_variants(void);
@@ -206,7 +207,8 @@ boys_status boys_eval_ragged_f64(const double *x, int64_t x_size, const int64_t 
  * arguments minus the workspace and uses a fixed scratch array compiled into
  * the library instead; it calls no allocation routine.
  *   - At most BOYS_RAGGED_NOALLOC_MAX_REQUESTS requests (the array holds the
- *     counters and the tile prefix for that many: about 512 KiB); more
+ *     counters, the tile prefix and the request order for that many: about
+ *     768 KiB); more
  *     returns BOYS_ERR_WORKSPACE before anything is launched.
  *   - The array exists once per GPU that loads the library and stays
  *     allocated until the process exits.

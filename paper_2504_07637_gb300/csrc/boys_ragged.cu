@@ -2,14 +2,20 @@
 // one graph-capturable call.
 //
 //   memset   zero the work counter and the error counter in the workspace
-//   plan     one block validates every request and prefix-sums its tile count
-//            into the workspace (tiles never straddle two requests, so each
-//            tile has a single n_max and runs its own fully unrolled kernel body)
+//   plan     one block validates every request, orders the requests by n_max
+//            (a counting sort, highest order first, invalid requests last)
+//            and prefix-sums their tile counts in that order into the
+//            workspace (tiles never straddle two requests, so each tile has a
+//            single n_max and runs its own fully unrolled kernel body)
 //   eval     persistent blocks (resident blocks x SMs) take the next tile with a
 //            global atomic, find its request by binary search in the tile
 //            prefix (copied to shared memory), and run the FP64 tile body of
 //            the plain path for that request's n_max.  Dynamic tile stealing
 //            balances requests whose cost differs by n_max and length.
+//
+// The order by n_max keeps the SMs on one or two of the 17 kernel bodies at a
+// time: taken in request order, every SM ran random orders, and instruction
+// fetch stalled a warp about 20 cycles per issued instruction (ncu).
 //
 // No host synchronisation and no allocation: the call can be captured in a
 // CUDA graph and replayed.  Arguments that only the device can read (the
@@ -36,13 +42,25 @@ struct RaggedArgs {
   double *out;
   int64_t out_size;
   int *counters;       // [1] invalid requests; [2..3] next tile (64-bit)
-  int64_t *tile_pref;  // [num_requests + 1]
+  int64_t *tile_pref;  // [num_requests + 1], over the requests in perm order
+  int32_t *perm;       // [num_requests]: the requests in the order their tiles run
 };
 
-// Workspace layout: 256 bytes of counters, then the int64 tile prefix.
+// Workspace layout: 256 bytes of counters, the int64 tile prefix, then the
+// int32 request order.
 __host__ __device__ inline int64_t *prefix_of(void *ws) {
   return reinterpret_cast<int64_t *>(static_cast<char *>(ws) + 256);
 }
+__host__ __device__ inline int32_t *perm_of(void *ws, int32_t num_requests) {
+  return reinterpret_cast<int32_t *>(prefix_of(ws) + num_requests + 1);
+}
+constexpr size_t ragged_ws_bytes(int32_t num_requests) {
+  return 256 + sizeof(int64_t) * ((size_t)num_requests + 1) + sizeof(int32_t) * (size_t)num_requests;
+}
+
+// Buckets of the request order: n_max = kRaggedMaxN first, down to 0, then
+// the invalid requests (whose tiles only fill NaN).
+constexpr int kRaggedBuckets = kRaggedMaxN + 2;
 
 // Tile count of request r for a given tile size, or the NaN-fill work of an
 // invalid request; *bad = 1 for an invalid request.
@@ -61,21 +79,46 @@ __device__ __forceinline__ int64_t request_tiles(const RaggedArgs &a, int r, int
 }
 
 template <int TILE>
+__device__ __forceinline__ int request_bucket(const RaggedArgs &a, int r) {
+  int bad = 0;
+  request_tiles<TILE>(a, r, &bad);
+  return bad ? kRaggedBuckets - 1 : kRaggedMaxN - a.n_max[r];
+}
+
+template <int TILE>
 __global__ void __launch_bounds__(kPlanThreads) ragged_plan_kernel(const RaggedArgs a) {
   __shared__ int64_t carry;
   __shared__ int64_t warp_sums[kPlanThreads / 32];
   __shared__ int bad_total;
+  __shared__ int hist[kRaggedBuckets], base[kRaggedBuckets];
   if (threadIdx.x == 0) {
     carry = 0;
     bad_total = 0;
     a.tile_pref[0] = 0;
   }
+  if (threadIdx.x < kRaggedBuckets) hist[threadIdx.x] = 0;
   __syncthreads();
+  // counting sort of the requests by bucket (the order within a bucket is
+  // arbitrary: each request writes only its own rows, so the results do not
+  // depend on it)
+  for (int r = threadIdx.x; r < a.num_requests; r += kPlanThreads) atomicAdd(&hist[request_bucket<TILE>(a, r)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 0; b < kRaggedBuckets; ++b) {
+      base[b] = acc;
+      acc += hist[b];
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < a.num_requests; r += kPlanThreads)
+    a.perm[atomicAdd(&base[request_bucket<TILE>(a, r)], 1)] = r;
+  __syncthreads();  // the block's writes of perm are visible to the block from here on
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r0 = 0; r0 < a.num_requests; r0 += kPlanThreads) {
-    const int r = r0 + threadIdx.x;
+  for (int i0 = 0; i0 < a.num_requests; i0 += kPlanThreads) {
+    const int i = i0 + threadIdx.x;
     int bad = 0;
-    int64_t v = r < a.num_requests ? request_tiles<TILE>(a, r, &bad) : 0;
+    int64_t v = i < a.num_requests ? request_tiles<TILE>(a, a.perm[i], &bad) : 0;
     if (bad) atomicAdd(&bad_total, 1);
     // inclusive block scan: warp shuffles, then the warp totals
     for (int d = 1; d < 32; d <<= 1) {
@@ -94,7 +137,7 @@ __global__ void __launch_bounds__(kPlanThreads) ragged_plan_kernel(const RaggedA
     }
     __syncthreads();
     const int64_t incl = v + (warp ? warp_sums[warp - 1] : 0) + carry;
-    if (r < a.num_requests) a.tile_pref[r + 1] = incl;
+    if (i < a.num_requests) a.tile_pref[i + 1] = incl;
     __syncthreads();
     if (threadIdx.x == kPlanThreads - 1) carry = incl;
     __syncthreads();
@@ -136,15 +179,15 @@ __global__ void __launch_bounds__(BLOCK) ragged_eval_kernel(const RaggedArgs a) 
     const int64_t t = sm.cur;
     __syncthreads();
     if (t >= total) break;
-    // request r with pref[r] <= t < pref[r+1]
+    // position i with pref[i] <= t < pref[i+1], request perm[i]
     int lo = 0, hi = R;
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
       if (pref[mid] <= t) lo = mid;
       else hi = mid;
     }
-    const int r = lo;
-    const int64_t k = t - pref[r];
+    const int r = a.perm[lo];
+    const int64_t k = t - pref[lo];
     int bad = 0;
     request_tiles<TILE>(a, r, &bad);
     if (bad) {
@@ -221,7 +264,7 @@ int boys_ragged_max_n(void) { return kRaggedMaxN; }
 
 size_t boys_ragged_workspace_bytes(int32_t num_requests) {
   if (num_requests < 0) return 0;
-  return 256 + sizeof(int64_t) * ((size_t)num_requests + 1);
+  return ragged_ws_bytes(num_requests);
 }
 
 boys_status boys_eval_ragged_f64(const double *x, int64_t x_size, const int64_t *offsets, const int32_t *n_max,
@@ -240,7 +283,7 @@ boys_status boys_eval_ragged_f64(const double *x, int64_t x_size, const int64_t 
       (reinterpret_cast<uintptr_t>(n_max) % 4))
     return BOYS_ERR_ALIGN;
   RaggedArgs a{x, x_size, offsets, n_max, out_offsets, num_requests, out, out_size,
-               static_cast<int *>(workspace), prefix_of(workspace)};
+               static_cast<int *>(workspace), prefix_of(workspace), perm_of(workspace, num_requests)};
   return (boys_status)kVariants[variant < 0 ? 0 : variant].launch(a, static_cast<cudaStream_t>(stream));
 }
 
@@ -265,8 +308,8 @@ boys_status boys_ragged_errors(const void *workspace, int64_t *n_bad_requests, v
 // host application whose device memory is all owned by its own pool and that
 // forbids libraries from calling cudaMalloc (an allocation can synchronise
 // the device and fragments the pool), or code running where no device
-// allocator is available to it.  For them the counters and tile prefix live
-// in one fixed array in the library's device image.  The array exists once
+// allocator is available to it.  For them the counters, the tile prefix and the
+// request order live in one fixed array in the library's device image.  The array exists once
 // per GPU that loads the library and stays allocated until the process
 // exits; every call shares it, so calls whose work overlaps on the GPU race
 // on it and must be ordered by the caller (for example, issued on one
@@ -275,7 +318,7 @@ boys_status boys_ragged_errors(const void *workspace, int64_t *n_bad_requests, v
 namespace {
 
 constexpr int32_t kNoAllocMaxRequests = BOYS_RAGGED_NOALLOC_MAX_REQUESTS;
-constexpr size_t kNoAllocScratchBytes = 256 + sizeof(int64_t) * ((size_t)kNoAllocMaxRequests + 1);
+constexpr size_t kNoAllocScratchBytes = ragged_ws_bytes(kNoAllocMaxRequests);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
