@@ -85,7 +85,7 @@ def test_ragged_host_argument_checks(capi):
     lib = capi.load()
     f = lib.boys_eval_ragged_f64
     need = lib.boys_ragged_workspace_bytes(10)
-    assert need == 256 + 8 * 11
+    assert need == 256 + 8 * 11 + 4 * 10  # counters, the tile prefix (R + 1) and the request order (R)
     # (x, x_size, offsets, n_max, out_offsets, R, out, out_size, ws, ws_bytes, variant, stream)
     assert f(8, 10, 8, 4, 8, -1, 8, 10, 256, need, -1, None) == 2  # R < 0
     assert f(8, 10, 8, 4, 8, 0, 8, 10, 256, need, -1, None) == 0  # empty batch
