@@ -863,11 +863,12 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
             "compute; host wall clock",
             # the host link bounds this number: plain pinned copies of the
             # same buffers, timed in the same run
-            "link_gbs": {"h2d": link["h2d_gbs"], "d2h": link["d2h_gbs"]},
-            "link_frac": round(max(t_h2d, t_d2h) / dt, 4),
+            "link_gbs": {"h2d": link["h2d_gbs"], "d2h": link["d2h_gbs"], "both": link["both_gbs"]},
+            "link_frac": round((h2d_b + d2h_b) / (link["both_gbs"] * 1e9) / dt, 4),
             "link_frac_serial": round((t_h2d + t_d2h) / dt, 4),
-            "link_note": "link_frac: the larger of the two plain copies (both directions at once) over the measured "
-            "step; link_frac_serial: the two copies one after the other",
+            "link_note": "link_frac: the same bytes copied in both directions at once (plain pinned copies of these "
+            "buffers, this run; on GB300 the two directions share the link's rate) over the measured step; "
+            "link_frac_serial: the two copies one after the other",
         }
         del xp, op, wsp
     del x, out
@@ -897,6 +898,25 @@ def link_rates(host_in, host_out, device):
             t = e0.elapsed_time(e1) / 1e3
             best = t if best is None else min(best, t)
         out[name] = round(nbytes / best / 1e9, 1)
+    # both directions at once (the host pipeline overlaps them): the link's
+    # total rate then, measured from the start of both to the end of both
+    side = torch.cuda.Stream(device)
+    best = None
+    for _ in range(3):
+        e0, e1, es = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        side.wait_event(e0)
+        with torch.cuda.stream(side):
+            dev_in.copy_(host_in, non_blocking=True)
+            es.record(side)
+        host_out.copy_(dev_out, non_blocking=True)
+        stream.wait_event(es)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    out["both_gbs"] = round((host_in.numel() * host_in.element_size() + host_out.numel() * host_out.element_size())
+                            / best / 1e9, 1)
     del dev_in, dev_out
     return out
 
