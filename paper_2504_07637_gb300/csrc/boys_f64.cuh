@@ -886,9 +886,12 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
   // list, and each then helps with the other one, so FP64-bound and
   // integer-bound requests run side by side instead of one list after
   // the other (n_max = 8: 139.5 -> 142.9 G values/s; two-point n_max = 36:
-  // 163.9 -> 171.5).  The staged one-point rows keep the plain order: there
-  // the two live phases cost registers and spills (n_max = 36: 200 -> 181).
-  constexpr bool MIX = !STAGED || TWO;
+  // 163.9 -> 171.5; staged one-point rows n_max = 12: 173.4 -> 181.4,
+  // 16: 191.2 -> 197.0, 20: 210.1 -> 210.9).  The staged one-point rows from
+  // n_max = 21 on keep the plain order: there the two live phases cost
+  // registers and instruction fetch (24: 220 -> 213, 28: 228 -> 208,
+  // 36: 251 -> 232).
+  constexpr bool MIX = !STAGED || TWO || NMAX <= 20;
   if constexpr (MIX) {
     const int par = (threadIdx.x >> 5) & 1;
 #pragma unroll 1
