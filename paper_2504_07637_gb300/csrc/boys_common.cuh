@@ -51,13 +51,14 @@ inline int persistent_grid(Kernel k, int block, size_t smem, int64_t tiles);
 // device (a kernel's attributes belong to the device's context, so one
 // process driving several GPUs needs them per device): the opt-in to
 // dyn_attr bytes of dynamic shared memory (0: none needed) and, when
-// want_grid, the persistent grid for dyn_smem bytes.  cache holds one slot
-// per device (0 = not set up).  Returns the grid (1 when !want_grid), or 0
-// on a CUDA error.
+// want_grid, the persistent grid for dyn_smem bytes.  carveout >= 0 sets the
+// kernel's preferred shared-memory share of the SM's on-chip memory (percent)
+// before the grid is sized.  cache holds one slot per device (0 = not set
+// up).  Returns the grid (1 when !want_grid), or 0 on a CUDA error.
 constexpr int kMaxCachedDevices = 64;
 template <typename Kernel>
 inline int device_setup(Kernel k, int block, size_t dyn_smem, size_t dyn_attr, bool want_grid,
-                        std::atomic<int> (&cache)[kMaxCachedDevices]) {
+                        std::atomic<int> (&cache)[kMaxCachedDevices], int carveout = -1) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   const bool cached = dev >= 0 && dev < kMaxCachedDevices;
@@ -66,6 +67,8 @@ inline int device_setup(Kernel k, int block, size_t dyn_smem, size_t dyn_attr, b
     if (g) return g;
   }
   if (dyn_attr > 0 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_attr) != cudaSuccess)
+    return 0;
+  if (carveout >= 0 && cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carveout) != cudaSuccess)
     return 0;
   const int g = want_grid ? persistent_grid(k, block, dyn_smem, INT64_MAX) : 1;
   if (cached) cache[dev].store(g, std::memory_order_release);

@@ -968,10 +968,22 @@ __device__ __forceinline__ void f64_tiles(const double *__restrict__ x, int64_t 
   }
 }
 
+// Resident blocks the unstaged kernels are compiled for.  The one-point row
+// kernels of 256 threads up to n_max = 9 ask for 8 (at most 32 registers;
+// with the largest shared-memory carveout, set at launch, 8 tiles of 22.6 KB
+// fit): 34 registers had left 6 blocks per SM, and n_max = 8 ran at 142.3 G
+// values/s against 145.7 with 8 (n_max = 4: 89.6 against 90.6), no spills.
+// From n_max = 10 on 32 registers spill.  The contraction and gradient
+// epilogues keep the default allocation.
+template <int NMAX, int BLOCK, typename MakeEpi, bool TWO>
+constexpr int f64_split_min_blocks() {
+  return (BLOCK == 256 && NMAX <= 9 && MakeEpi::kRows && !TWO) ? 8 : 1;
+}
+
 // Plain, gradient and contraction kernels: persistent blocks stride over the tiles.
 template <int NMAX, int BLOCK, int TILE, typename MakeEpi, bool TWO = false>
-__global__ void __launch_bounds__(BLOCK) f64_split_kernel(const double *__restrict__ x, int64_t count,
-                                                          const MakeEpi make) {
+__global__ void __launch_bounds__(BLOCK, (f64_split_min_blocks<NMAX, BLOCK, MakeEpi, TWO>()))
+    f64_split_kernel(const double *__restrict__ x, int64_t count, const MakeEpi make) {
   __shared__ F64TileSmem<TILE, true> sm;
   f64_tiles<NMAX, BLOCK, TILE, MakeEpi, TWO, 0, 1>(x, count, make, sm, nullptr);
 }
@@ -989,6 +1001,7 @@ __global__ void __launch_bounds__(BLOCK, (f64_min_blocks<BLOCK, TILE, STAGE, K>(
 
 template <int W>
 struct MakeStore {
+  static constexpr bool kRows = true;
   double *out;
   __device__ __forceinline__ void prepare() {}
   __device__ __forceinline__ StoreRows<W> operator()(int64_t base) const { return StoreRows<W>{out + base * W}; }
@@ -996,6 +1009,7 @@ struct MakeStore {
 
 template <int W>
 struct MakeGrad {
+  static constexpr bool kRows = false;
   const double *g;
   int64_t g_row, g_col;
   double *grad;
@@ -1020,6 +1034,7 @@ struct MakeGrad {
 
 template <int W>
 struct MakeContract {
+  static constexpr bool kRows = false;
   const double *c;
   int64_t c_row, c_col;
   double *out;
@@ -1052,8 +1067,8 @@ constexpr int kF64SmallBlock = 128, kF64SmallTile = 256;
 // Launch kernel k on a persistent grid (set up per device through cache).
 template <typename Kernel, typename MakeEpi>
 int launch_f64_persistent(Kernel k, std::atomic<int> (&cache)[kMaxCachedDevices], int block, int tile, size_t dyn,
-                          const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s) {
-  const int grid_cap = device_setup(k, block, dyn, dyn, true, cache);
+                          const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s, int carveout = -1) {
+  const int grid_cap = device_setup(k, block, dyn, dyn, true, cache, carveout);
   if (grid_cap == 0) return BOYS_ERR_CUDA;
   const int64_t tiles = (count + tile - 1) / tile;
   const int grid = (int)(tiles < grid_cap ? tiles : grid_cap);
@@ -1068,8 +1083,11 @@ int launch_f64_shape(const double *x, int64_t count, const MakeEpi &epi, cudaStr
     return launch_f64_persistent(f64_staged_kernel<NMAX, BLOCK, TILE, MakeEpi, TWO, STAGE, K>, cache, BLOCK, TILE,
                                  f64_stage_bytes<BLOCK, STAGE, K>(), x, count, epi, s);
   } else {
+    // compiled for 8 resident blocks: all of the SM's on-chip memory that
+    // can be shared memory, as their tiles take more than the default split
+    constexpr bool eight = f64_split_min_blocks<NMAX, BLOCK, MakeEpi, TWO>() == 8;
     return launch_f64_persistent(f64_split_kernel<NMAX, BLOCK, TILE, MakeEpi, TWO>, cache, BLOCK, TILE, 0, x,
-                                 count, epi, s);
+                                 count, epi, s, eight ? 100 : -1);
   }
 }
 
