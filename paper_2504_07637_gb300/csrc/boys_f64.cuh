@@ -377,18 +377,24 @@ __device__ __forceinline__ void f64_recurse_staged(const double (&f0)[K], const 
       }
     });
   } else {
-    // On the integer pipes.  Whole chunks of CH orders that are all staged,
-    // flushed in full and above LO - 1 run in a loop over the chunks (an
-    // integer step is ~36 instructions, and unrolled over every order the
-    // code of the high orders outgrew the instruction cache); the orders
-    // above them (from TOP) and below them (down to LO) are unrolled.
+    // On the integer pipes.  An integer step is ~36 instructions, and the
+    // code size sets the pace here: one order per loop iteration wherever the
+    // chunks allow it.  Whole chunks of CH orders that are all staged, flushed
+    // in full and above LO - 1 run in a loop over the chunks, and so do the
+    // orders above them, from TOP (no multiple of CH among them but the
+    // lowest, MT); without a whole chunk (TOP < 2 CH) and below the lowest one
+    // (down to LO) the orders are unrolled.  Unrolled over every order, the
+    // code of the high orders outgrew the instruction cache; with the chunks
+    // looped and their 16 orders unrolled, n_max = 24 / 28 / 36 ran at
+    // 220.6 / 228.4 / 251.5 G values/s, one order per iteration (with warps
+    // starting on alternating lists, f64_tile) 238.7 / 249.3 / 280.4.
     Sig64Down r[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) r[k].start(f0[k], tx[k], e[k]);
     constexpr int TOPM = HI < TOP - 1 ? HI : TOP - 1;  // highest order a looped chunk may hold
     constexpr int CT = (TOPM + 1) / CH - 1;            // highest such chunk
     constexpr int CB = (LO + CH - 1) / CH;             // lowest chunk that starts at or above LO
-    constexpr int MT = CT >= CB ? CH * (CT + 1) : LO;  // orders TOP .. MT unrolled before the loop
+    constexpr int MT = CT >= CB ? CH * (CT + 1) : LO;  // orders TOP .. MT come before the chunks
     auto unrolled = [&](auto mc) {
       constexpr int m = decltype(mc)::value;
       if constexpr (m <= HI) {
@@ -402,23 +408,42 @@ __device__ __forceinline__ void f64_recurse_staged(const double (&f0)[K], const 
         for (int k = 0; k < K; ++k) r[k].template step<m>();
       }
     };
-    static_for<TOP, MT - 1, -1>(unrolled);
     if constexpr (CT >= CB) {
+      // orders TOP .. MT + 1 (MT >= CH, so no step of order 1 here: the run
+      // time step equals the unrolled one bit for bit, and F_TOP rounds back
+      // to f0 exactly)
+#pragma unroll 1
+      for (int m = TOP; m > MT; --m) {
+        if (m <= HI) {
+#pragma unroll
+          for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + (m - MT)] = r[k].value();
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) r[k].step_rt(m);
+      }
+      static_for<MT, MT - 1, -1>(unrolled);
 #pragma unroll 1
       for (int c = CT; c >= CB; --c) {
         const int m0 = c * CH;
-#pragma unroll
-        for (int i = CH - 1; i >= 0; --i) {
+        // m0 >= LO, so every order above m0 steps
+#pragma unroll 1
+        for (int i = CH - 1; i >= 1; --i) {
 #pragma unroll
           for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + i] = r[k].value();
-          if (i == 0) f64_stage_flush<W, CH, K, CH>(out, stg, m0, j, lane);
-          if (m0 + i > LO) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) r[k].step_rt(m0 + i);
-          }
+          for (int k = 0; k < K; ++k) r[k].step_rt(m0 + i);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch] = r[k].value();
+        f64_stage_flush<W, CH, K, CH>(out, stg, m0, j, lane);
+        if (m0 > LO) {
+#pragma unroll
+          for (int k = 0; k < K; ++k) r[k].step_rt(m0);
         }
       }
       static_for<CH * CB - 1, LO - 1, -1>(unrolled);
+    } else {
+      static_for<TOP, LO - 1, -1>(unrolled);
     }
   }
 }
@@ -472,8 +497,9 @@ __device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const
     ok = ok && sig64_chain_ok<NMAX>(x[k]);
   }
   if (__all_sync(0xffffffffu, ok)) {
-    // the first chunk of CH orders and the partial last one unrolled, the
-    // whole chunks between them in a loop (as in f64_recurse_staged)
+    // one order per loop iteration, as in f64_recurse_staged: the whole
+    // chunks of CH orders, then the partial last one (the run-time step
+    // equals the unrolled one bit for bit); rows shorter than CH unrolled
     Sig64Chain ch[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) ch[k].start(f[k], y[k]);
@@ -487,18 +513,36 @@ __device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const
       if constexpr (m % CH == CH - 1 || m == NMAX) f64_stage_flush<W, CH, K, m % CH + 1>(out, stg, m - m % CH, j, lane);
     };
     constexpr int CF = W / CH - 1;  // highest whole chunk
-    static_for<0, (W < CH ? W : CH), 1>(unrolled);
+    if constexpr (CF >= 0) {
 #pragma unroll 1
-    for (int c = 1; c <= CF; ++c) {
-      const int m0 = c * CH;
+      for (int c = 0; c <= CF; ++c) {
+        const int m0 = c * CH;
+        if (c == 0) {
 #pragma unroll
-      for (int i = 0; i < CH; ++i) {
+          for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch] = f[k];
+        } else {
 #pragma unroll
-        for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + i] = ch[k].next_rt(m0 + i);
+          for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch] = ch[k].next_rt(m0);
+        }
+#pragma unroll 1
+        for (int i = 1; i < CH; ++i) {
+#pragma unroll
+          for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + i] = ch[k].next_rt(m0 + i);
+        }
+        f64_stage_flush<W, CH, K, CH>(out, stg, m0, j, lane);
       }
-      f64_stage_flush<W, CH, K, CH>(out, stg, m0, j, lane);
+      constexpr int MB = (CF + 1) * CH;  // the partial last chunk
+      if constexpr (MB < W) {
+#pragma unroll 1
+        for (int m = MB; m < W; ++m) {
+#pragma unroll
+          for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + (m - MB)] = ch[k].next_rt(m);
+        }
+        f64_stage_flush<W, CH, K, W - MB>(out, stg, MB, j, lane);
+      }
+    } else {
+      static_for<0, W, 1>(unrolled);
     }
-    static_for<(CF + 1 > 1 ? CF + 1 : 1) * CH, W, 1>(unrolled);
     return;
   }
   // beyond the integer chain's range (x > 2^27 at n_max = 36; none of the
@@ -887,24 +931,19 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
   // integer-bound requests run side by side instead of one list after
   // the other (n_max = 8: 139.5 -> 142.9 G values/s; two-point n_max = 36:
   // 163.9 -> 171.5; staged one-point rows n_max = 12: 173.4 -> 181.4,
-  // 16: 191.2 -> 197.0, 20: 210.1 -> 210.9).  The staged one-point rows from
-  // n_max = 21 on keep the plain order: there the two live phases cost
-  // registers and instruction fetch (24: 220 -> 213, 28: 228 -> 208,
-  // 36: 251 -> 232).
-  constexpr bool MIX = !STAGED || TWO || NMAX <= 20;
-  if constexpr (MIX) {
-    const int par = (threadIdx.x >> 5) & 1;
+  // 16: 191.2 -> 197.0, 20: 210.1 -> 210.9).  From n_max = 21 on it pays
+  // only since the integer chains loop over single orders (measured with two
+  // orders per iteration, 24: 219.3 -> 239.9, 32: 254.8 -> 276.9, 36: 259.8
+  // -> 277.2); with their 16 orders unrolled the two live phases had cost
+  // instruction fetch (36: 251 -> 232).
+  const int par = (threadIdx.x >> 5) & 1;
 #pragma unroll 1
-    for (int ph = 0; ph < 2; ++ph) {
-      if ((ph ^ par) == 0) {
-        below_loop();
-      } else {
-        above_loop();
-      }
+  for (int ph = 0; ph < 2; ++ph) {
+    if ((ph ^ par) == 0) {
+      below_loop();
+    } else {
+      above_loop();
     }
-  } else {
-    below_loop();
-    above_loop();
   }
   __syncthreads();
   if constexpr (CARRY) {
