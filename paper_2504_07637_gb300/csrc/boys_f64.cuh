@@ -318,13 +318,19 @@ __device__ __forceinline__ void f64_asymptote(const double x, double (&F)[NMAX +
 // Staged row stores.  A warp whose lanes hold K list entries each (32 K
 // rows) would store F_m from 32 lanes into 32 sectors (the rows are n_max+1
 // doubles apart).  Instead it collects F_m for CH consecutive m of its rows in
-// shared memory (odd row pitch: conflict-free 64-bit lane access) and writes
-// each 32K x LEN block with consecutive lanes on consecutive elements of a
-// row: a store instruction covers 32 / LEN row segments of LEN doubles.
+// shared memory and writes each 32K x LEN block with consecutive lanes on
+// consecutive elements of a row: a store instruction covers 32 / LEN row
+// segments of LEN doubles.  Bank conflicts: with CH a power of two from 16
+// on, rows are CH doubles and column c of row r sits at c ^ (r mod 16), so
+// that 16 lanes writing one column of 16 rows, or reading 16 columns of one
+// row, meet 16 different bank pairs; otherwise the row pitch is odd.  The
+// unpadded rows let four blocks of 256 threads share an SM (f64_min_blocks).
 template <int CH, int K>
 struct F64Stage {
-  static constexpr int kPitch = CH | 1;
+  static constexpr bool kSwizzle = CH >= 16 && (CH & (CH - 1)) == 0;
+  static constexpr int kPitch = kSwizzle ? CH : (CH | 1);
   static constexpr int kDoublesPerWarp = 32 * K * kPitch;
+  __device__ static __forceinline__ int at(int r, int c) { return r * kPitch + (kSwizzle ? (c ^ (r & 15)) : c); }
 };
 
 // The row index comes from a volatile shuffle: the addresses of a flush are
@@ -347,7 +353,7 @@ __device__ __forceinline__ void f64_stage_flush(double *__restrict__ out, const 
     const int f = 32 * t + lane;
     const int r = f / LEN, e = f - r * LEN;
     const int jr = shfl_idx_volatile(j[t / LEN], r & 31);
-    if (jr != kNoRow) __stcs(out + ((int64_t)jr * W + (m0 + e)), stg[r * F64Stage<CH, K>::kPitch + e]);
+    if (jr != kNoRow) __stcs(out + ((int64_t)jr * W + (m0 + e)), stg[F64Stage<CH, K>::at(r, e)]);
   }
   __syncwarp();
 }
@@ -368,7 +374,7 @@ __device__ __forceinline__ void f64_recurse_staged(const double (&f0)[K], const 
       constexpr int m = decltype(mc)::value;
       if constexpr (m <= HI) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + m % CH] = f[k];
+        for (int k = 0; k < K; ++k) stg[F64Stage<CH, K>::at(32 * k + lane, m % CH)] = f[k];
         if constexpr (m % CH == 0) f64_stage_flush<W, CH, K, (W - m < CH ? W - m : CH)>(out, stg, m, j, lane);
       }
       if constexpr (m > LO) {
@@ -400,7 +406,7 @@ __device__ __forceinline__ void f64_recurse_staged(const double (&f0)[K], const 
       if constexpr (m <= HI) {
 #pragma unroll
         for (int k = 0; k < K; ++k)
-          stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + m % CH] = m == TOP ? f0[k] : r[k].value();
+          stg[F64Stage<CH, K>::at(32 * k + lane, m % CH)] = m == TOP ? f0[k] : r[k].value();
         if constexpr (m % CH == 0) f64_stage_flush<W, CH, K, (W - m < CH ? W - m : CH)>(out, stg, m, j, lane);
       }
       if constexpr (m > LO) {
@@ -416,7 +422,7 @@ __device__ __forceinline__ void f64_recurse_staged(const double (&f0)[K], const 
       for (int m = TOP; m > MT; --m) {
         if (m <= HI) {
 #pragma unroll
-          for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + (m - MT)] = r[k].value();
+          for (int k = 0; k < K; ++k) stg[F64Stage<CH, K>::at(32 * k + lane, (m - MT))] = r[k].value();
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) r[k].step_rt(m);
@@ -429,12 +435,12 @@ __device__ __forceinline__ void f64_recurse_staged(const double (&f0)[K], const 
 #pragma unroll 1
         for (int i = CH - 1; i >= 1; --i) {
 #pragma unroll
-          for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + i] = r[k].value();
+          for (int k = 0; k < K; ++k) stg[F64Stage<CH, K>::at(32 * k + lane, i)] = r[k].value();
 #pragma unroll
           for (int k = 0; k < K; ++k) r[k].step_rt(m0 + i);
         }
 #pragma unroll
-        for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch] = r[k].value();
+        for (int k = 0; k < K; ++k) stg[F64Stage<CH, K>::at(32 * k + lane, 0)] = r[k].value();
         f64_stage_flush<W, CH, K, CH>(out, stg, m0, j, lane);
         if (m0 > LO) {
 #pragma unroll
@@ -508,7 +514,7 @@ __device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if constexpr (m > 0) f[k] = ch[k].template next<m>();
-        stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + m % CH] = f[k];
+        stg[F64Stage<CH, K>::at(32 * k + lane, m % CH)] = f[k];
       }
       if constexpr (m % CH == CH - 1 || m == NMAX) f64_stage_flush<W, CH, K, m % CH + 1>(out, stg, m - m % CH, j, lane);
     };
@@ -519,15 +525,15 @@ __device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const
         const int m0 = c * CH;
         if (c == 0) {
 #pragma unroll
-          for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch] = f[k];
+          for (int k = 0; k < K; ++k) stg[F64Stage<CH, K>::at(32 * k + lane, 0)] = f[k];
         } else {
 #pragma unroll
-          for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch] = ch[k].next_rt(m0);
+          for (int k = 0; k < K; ++k) stg[F64Stage<CH, K>::at(32 * k + lane, 0)] = ch[k].next_rt(m0);
         }
 #pragma unroll 1
         for (int i = 1; i < CH; ++i) {
 #pragma unroll
-          for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + i] = ch[k].next_rt(m0 + i);
+          for (int k = 0; k < K; ++k) stg[F64Stage<CH, K>::at(32 * k + lane, i)] = ch[k].next_rt(m0 + i);
         }
         f64_stage_flush<W, CH, K, CH>(out, stg, m0, j, lane);
       }
@@ -536,7 +542,7 @@ __device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const
 #pragma unroll 1
         for (int m = MB; m < W; ++m) {
 #pragma unroll
-          for (int k = 0; k < K; ++k) stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + (m - MB)] = ch[k].next_rt(m);
+          for (int k = 0; k < K; ++k) stg[F64Stage<CH, K>::at(32 * k + lane, (m - MB))] = ch[k].next_rt(m);
         }
         f64_stage_flush<W, CH, K, W - MB>(out, stg, MB, j, lane);
       }
@@ -558,7 +564,7 @@ __device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (m > 0) f[k] = f[k] * ((double(m) - 0.5) * y[k]);
-        stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + i] = f[k];
+        stg[F64Stage<CH, K>::at(32 * k + lane, i)] = f[k];
       }
     }
     f64_stage_flush<W, CH, K, CH>(out, stg, m0, j, lane);
@@ -568,7 +574,7 @@ __device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if constexpr (m > 0) f[k] = f[k] * ((double(m) - 0.5) * y[k]);
-      stg[(32 * k + lane) * F64Stage<CH, K>::kPitch + m % CH] = f[k];
+      stg[F64Stage<CH, K>::at(32 * k + lane, m % CH)] = f[k];
     }
     if constexpr (m == NMAX) f64_stage_flush<W, CH, K, m % CH + 1>(out, stg, m - m % CH, j, lane);
   });
@@ -982,7 +988,13 @@ constexpr size_t f64_stage_bytes() {
 
 // Resident blocks per SM that a staged kernel is compiled for: as many as its
 // shared memory allows (228 KB per SM, 1 KB reserved per block), at most 4;
-// the register budget follows from it.
+// the register budget follows from it.  Blocks of 256 threads with 2048-
+// argument tiles take 55.4 KB: 4 blocks of 64 registers.  Against 3 blocks
+// of 80 registers with odd-pitch rows (57.4 KB), n_max = 20 / 24 / 28 / 32 /
+// 36 measured 223.8 / 238.2 / 249.1 / 275.6 / 279.9 -> 227.3 / 242.7 /
+// 257.5 / 281.9 / 280.7 G values/s, two-point n_max = 36 175.6 -> 174.6.
+// (With the integer chains' 16 orders unrolled per chunk, 4 blocks had
+// been slower: 251.7 -> 238.5 at n_max = 36.)
 template <int BLOCK, int TILE, int STAGE, int K>
 constexpr int f64_min_blocks() {
   if (STAGE == 0) return 1;
