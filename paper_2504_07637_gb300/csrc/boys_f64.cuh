@@ -256,20 +256,38 @@ __device__ __forceinline__ bool sig64_chain_ok(const double x) {
   return (unsigned long long)__double_as_longlong(x) < sig64_chain_xmax_bits(NMAX);
 }
 
-// The asymptote of f64_asymptote_fp64 with its product chain on the integer
-// pipes (boys_sig64.cuh): F_0 = c_0 rsqrt(x) and y = 1/x in FP64, then
-// z_m = F_0 y^m and F_m = z_m prod_{k<=m} (k - 1/2) as 64-bit significands,
-// each F_m rounded once.  Requires sig64_chain_ok<NMAX>(x).
+// The start of the asymptote on the integer pipes, for x above the cut-off
+// with sig64_chain_ok<n_max>(x): r = 1/sqrt(x) by sig64_rsqrt (seeded by
+// the float rsqrtf of x's leading bits), then F_0 = c_0 r and y = r^2 = 1/x
+// as 64-bit significands (within 2^-59 of their values); F_0 rounded to a
+// double is returned.  In FP64 these cost a reciprocal square root and, for
+// the high orders' y, a division: about 5 and 7.6 FMA times on the FP64
+// pipe, which bounds the kernels.
+__device__ __forceinline__ double f64_asymptote_start(const double x, uint64_t &sf, int &ef, uint64_t &sy, int &ey) {
+  const uint64_t xb = (uint64_t)__double_as_longlong(x);
+  int k;
+  const uint32_t ab = sig64_rsqrt_reduce(xb, k);
+  uint64_t sr;
+  int er;
+  sig64_rsqrt(xb, __float_as_uint(rsqrtf(__uint_as_float(ab))), sr, er);
+  sy = sr;
+  ey = er;
+  sig64_mul(sy, ey, sr, er);
+  sf = kSig64C0s;
+  ef = kSig64C0e;
+  sig64_mul(sf, ef, sr, er);
+  return __longlong_as_double((long long)sig64_round_bits(sf, ef));
+}
+
+// The asymptote of f64_asymptote_fp64 on the integer pipes (boys_sig64.cuh):
+// F_0 and y = 1/x from f64_asymptote_start, then z_m = F_0 y^m and
+// F_m = z_m prod_{k<=m} (k - 1/2) as 64-bit significands, each F_m rounded
+// once.  Requires sig64_chain_ok<NMAX>(x).
 struct Sig64Chain {
   uint64_t s, sy;
   int e, ey;
-  __device__ __forceinline__ void start(const double f0, const double y) {
-    const uint64_t fb = __double_as_longlong(f0), yb = __double_as_longlong(y);
-    s = sig64_of_bits(fb);
-    e = exp_of_bits(fb);
-    sy = sig64_of_bits(yb);
-    ey = exp_of_bits(yb);
-  }
+  // F_0 (returned) and the chain's start
+  __device__ __forceinline__ double start(const double x) { return f64_asymptote_start(x, s, e, sy, ey); }
   // z_m from z_{m-1}, and F_m
   template <int M>
   __device__ __forceinline__ double next() {
@@ -292,11 +310,9 @@ struct Sig64Chain {
 
 template <int NMAX>
 __device__ __forceinline__ void f64_asymptote_int(const double x, double (&F)[NMAX + 1]) {
-  const double rs = rsqrt(x);
-  F[0] = 0.88622692545275801365 * rs;
+  Sig64Chain ch;
+  F[0] = ch.start(x);
   if constexpr (NMAX >= 1) {
-    Sig64Chain ch;
-    ch.start(F[0], NMAX <= 12 ? rs * rs : 1.0 / x);
     static_for<1, NMAX + 1, 1>([&](auto mc) {
       constexpr int m = decltype(mc)::value;
       F[m] = ch.template next<m>();
@@ -308,10 +324,28 @@ __device__ __forceinline__ void f64_asymptote_int(const double x, double (&F)[NM
 // (every argument of the benchmark distributions), else in FP64.
 template <int NMAX>
 __device__ __forceinline__ void f64_asymptote(const double x, double (&F)[NMAX + 1]) {
-  if (NMAX >= 1 && sig64_chain_ok<NMAX>(x)) {
+  if (sig64_chain_ok<NMAX>(x)) {
     f64_asymptote_int<NMAX>(x, F);
   } else {
     f64_asymptote_fp64<NMAX>(x, F);
+  }
+}
+
+// F_0 and y = 1/x of the asymptote as doubles (the Horner forms of the fused
+// consumers): from f64_asymptote_start where the chain's range allows, else
+// in FP64.  y is left 0 for NMAX = 0, where nothing uses it (and 1/x may be
+// subnormal).
+template <int NMAX>
+__device__ __forceinline__ void f64_asymptote_f0_y(const double x, double &f0, double &y) {
+  if (sig64_chain_ok<NMAX>(x)) {
+    uint64_t sf, sy;
+    int ef, ey;
+    f0 = f64_asymptote_start(x, sf, ef, sy, ey);
+    y = NMAX >= 1 ? __longlong_as_double((long long)sig64_round_bits(sy, ey)) : 0.0;
+  } else {
+    const double rs = rsqrt(x);
+    f0 = 0.88622692545275801365 * rs;
+    y = NMAX <= 12 ? rs * rs : 1.0 / x;
   }
 }
 
@@ -493,22 +527,17 @@ __device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const
                                                      double *__restrict__ out, double *__restrict__ stg,
                                                      const int lane) {
   constexpr int W = NMAX + 1;
-  double f[K], y[K];
+  double f[K];
   bool ok = true;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const double rs = rsqrt(x[k]);
-    f[k] = 0.88622692545275801365 * rs;
-    y[k] = NMAX <= 12 ? rs * rs : 1.0 / x[k];
-    ok = ok && sig64_chain_ok<NMAX>(x[k]);
-  }
+  for (int k = 0; k < K; ++k) ok = ok && sig64_chain_ok<NMAX>(x[k]);
   if (__all_sync(0xffffffffu, ok)) {
     // one order per loop iteration, as in f64_recurse_staged: the whole
     // chunks of CH orders, then the partial last one (the run-time step
     // equals the unrolled one bit for bit); rows shorter than CH unrolled
     Sig64Chain ch[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) ch[k].start(f[k], y[k]);
+    for (int k = 0; k < K; ++k) f[k] = ch[k].start(x[k]);
     auto unrolled = [&](auto mc) {
       constexpr int m = decltype(mc)::value;
 #pragma unroll
@@ -554,6 +583,13 @@ __device__ __forceinline__ void f64_asymptote_staged(const double (&x)[K], const
   // beyond the integer chain's range (x > 2^27 at n_max = 36; none of the
   // benchmark arguments): the FP64 chain, looped over whole chunks to keep
   // the code small
+  double y[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double rs = rsqrt(x[k]);
+    f[k] = 0.88622692545275801365 * rs;
+    y[k] = NMAX <= 12 ? rs * rs : 1.0 / x[k];
+  }
   constexpr int CF = W / CH - 1;  // highest whole chunk (-1 if none)
 #pragma unroll 1
   for (int c = 0; c <= CF; ++c) {
@@ -626,15 +662,15 @@ struct GradDot {
   }
   __device__ __forceinline__ bool uniform() const { return g_row == 0; }
   // Above the cut-off F_{m+1} = F_0 prod_{k<=m+1} (k - 1/2) y^{m+1}, so the
-  // gradient is -F_0 y P(y) by Horner (uniform weights only); the same 1/x
-  // and rsqrt forms as f64_asymptote.
+  // gradient is -F_0 y P(y) by Horner (uniform weights only), with F_0 and
+  // y as f64_asymptote forms them.
   __device__ __forceinline__ double asymptote_dot(const double x) const {
-    const double rs = rsqrt(x);
-    const double y = W - 1 <= 12 ? rs * rs : 1.0 / x;
+    double f0, y;
+    f64_asymptote_f0_y<W - 1>(x, f0, y);
     double acc = hu[W - 2];
 #pragma unroll
     for (int m = W - 3; m >= 0; --m) acc = fma(acc, y, hu[m]);
-    return -(acc * ((0.88622692545275801365 * rs) * y));
+    return -(acc * (f0 * y));
   }
   __device__ __forceinline__ void put(int j, double v) const { grad[j] = v; }
 };
@@ -663,15 +699,15 @@ struct ContractDot {
   }
   __device__ __forceinline__ bool uniform() const { return c_row == 0; }
   // Above the cut-off, where F_m = F_0 prod_{k<=m} (k - 1/2) y: the
-  // contraction is F_0 P(y) by Horner (uniform coefficients only); the same
-  // 1/x and rsqrt forms as f64_asymptote.
+  // contraction is F_0 P(y) by Horner (uniform coefficients only), with F_0
+  // and y as f64_asymptote forms them.
   __device__ __forceinline__ double asymptote_dot(const double x) const {
-    const double rs = rsqrt(x);
-    const double y = W - 1 <= 12 ? rs * rs : 1.0 / x;
+    double f0, y;
+    f64_asymptote_f0_y<W - 1>(x, f0, y);
     double acc = hu[W - 1];
 #pragma unroll
     for (int m = W - 2; m >= 0; --m) acc = fma(acc, y, hu[m]);
-    return acc * (0.88622692545275801365 * rs);
+    return acc * f0;
   }
   __device__ __forceinline__ void put(int j, double v) const { out[j] = v; }
 };

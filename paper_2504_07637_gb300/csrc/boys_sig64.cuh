@@ -89,6 +89,65 @@ BOYS_HD uint64_t sig64_round_bits(uint64_t s, int e) {
   return m + ((uint64_t)(e + 1022) << 52);
 }
 
+// 1/sqrt(x) for a positive normal double x, by Newton's method on 64-bit
+// significands.  Write x = a 4^k with a in [1, 4).  sig64_rsqrt_reduce gives
+// k and the bits of a float holding a's leading 24 bits, whose reciprocal
+// square root (a float approximation, e.g. the device's rsqrtf) seeds r;
+// sig64_rsqrt then takes two steps r <- r (1 + d/2), d = 1 - a r^2, each of
+// which maps a relative error eps to about 3 eps^2 / 2 (2^-20 -> 2^-39 ->
+// 2^-77).  d is formed in fixed point from t = a r^2, which the products leave
+// within 2^-18 of 1: |d| 2^64 < 2^46 as a signed integer.  The products add
+// relative errors below 2^-62 each, so the result is within 2^-60 of
+// 1/sqrt(x) for a seed within 2^-20 of 1/sqrt(a).
+BOYS_HD uint32_t sig64_rsqrt_reduce(uint64_t xbits, int &k) {
+  const int ex = exp_of_bits(xbits);
+  const int p = ex & 1;  // ex = 2k + p, also for negative ex (two's complement)
+  k = (ex - p) / 2;
+  return ((uint32_t)(127 + p) << 23) | (uint32_t)((xbits >> 29) & 0x7fffffu);
+}
+
+BOYS_HD void sig64_rsqrt(uint64_t xbits, uint32_t seed_bits, uint64_t &s, int &e) {
+  const int ex = exp_of_bits(xbits);
+  const int p = ex & 1;
+  const int k = (ex - p) / 2;
+  const uint64_t sa = sig64_of_bits(xbits);  // a = sa 2^(p - 63)
+  uint64_t sr = (uint64_t)((seed_bits & 0x7fffffu) | 0x800000u) << 40;
+  int er = (int)((seed_bits >> 23) & 0xffu) - 127;
+  for (int it = 0; it < 2; ++it) {
+    uint64_t t = sr;
+    int et = er;
+    sig64_mul(t, et, sr, er);
+    sig64_mul(t, et, sa, p);
+    // d 2^64 from t 2^(et - 63), et being -1 (t < 1) or 0 (t >= 1)
+    const int64_t d = et == 0 ? -(int64_t)((t - (1ull << 63)) << 1) : (int64_t)(0ull - t);
+    const uint64_t c = mulhi_trunc(sr, d < 0 ? (uint64_t)(-d) : (uint64_t)d) >> 1;  // r |d| / 2
+    if (d >= 0) {
+      const uint64_t u = sr + c;
+      if (u < sr) {  // carried out: r crossed a power of two upwards
+        sr = (u >> 1) | (1ull << 63);
+        er += 1;
+      } else {
+        sr = u;
+      }
+    } else {
+      const uint64_t u = sr - c;
+      if (u < (1ull << 63)) {  // r crossed a power of two downwards
+        sr = u << 1;
+        er -= 1;
+      } else {
+        sr = u;
+      }
+    }
+  }
+  s = sr;
+  e = er - k;
+}
+
+// c_0 = sqrt(pi)/2 (Eq. "limf1": F_0 = c_0 / sqrt(x) above the cut-off),
+// rounded to 64 bits: 0.886226925452758013649... = 0xe2dfc48da77b553d 2^-64.
+constexpr uint64_t kSig64C0s = 0xe2dfc48da77b553dull;
+constexpr int kSig64C0e = -1;
+
 // prod_{k=1}^{m} (k - 1/2) = (2m - 1)!! / 2^m as a Sig64, each factor
 // applied exactly and the product rounded to 64 bits (relative error below
 // m 2^-64).  (2k - 1) s needs at most 71 bits, held as hi 2^32 + lo.

@@ -6,9 +6,11 @@ exponential (shared with the recursion, Eq. "r"), the half-integer powers
 Q^{n+1/2} and D^{-(n+1/2)} as square-and-multiply plus a reciprocal square
 root each, and two operations per step of the downward recursion (on the
 integer pipes instead in the row kernels, and for recursions of up to 18
-steps elsewhere); above it (Eq.
-"limf1") one reciprocal square root, F_0 and 1/x, the upward product chain
-running on the integer pipes.  "fma" counts every add, multiply or
+steps elsewhere); above it (Eq. "limf1") nothing on the FP64 pipe: F_0 and
+1/x come from a reciprocal square root by Newton steps on 64-bit integer
+significands, and the upward product chain runs there too.  The all-FP64
+form (int_chain=False) counts one reciprocal square root, F_0, 1/x and the
+chain's two products per order instead.  "fma" counts every add, multiply or
 fused multiply-add (each one FP64-pipe instruction).  Bytes per argument are
 the input value plus the n_max+1 outputs.
 """
@@ -59,21 +61,28 @@ def _closed_form_counts(n_top: int) -> dict:
     return {"fma": fma, "div": div, "sqrt": 0, "exp": 0, "rsqrt": rsq}
 
 
+_NONE = {"fma": 0, "div": 0, "sqrt": 0, "exp": 0, "rsqrt": 0}
+
+
+def _asymptote_start_fp64(n_max: int) -> dict:
+    """F_0 = c_0 rsqrt(x) and y = 1/x in FP64: one reciprocal square root,
+    one product, y as rsqrt(x)^2 for n_max <= 12, else a division."""
+    return {"fma": 1 + (1 if 1 <= n_max <= 12 else 0), "div": 1 if n_max > 12 else 0, "sqrt": 0, "exp": 0,
+            "rsqrt": 1}
+
+
 def _asymptote_counts(n_max: int, int_chain: bool = True) -> dict:
-    """FP64 operations of the asymptote row (Eq. "limf1"): one reciprocal
-    square root, F_0 = c_0 rsqrt(x), 1/x as rsqrt(x)^2 for n_max <= 12 (else
-    a division), and the upward chain F_m = F_{m-1} (m - 1/2) / x.  The
-    kernels run that chain on 64-bit integer significands (csrc/boys_sig64.cuh),
-    which leaves the FP64 pipe with F_0 and 1/x only; int_chain=False counts
-    it as two FP64 multiplications per order instead."""
-    y = 0 if n_max == 0 else (1 if n_max <= 12 else 0)
-    return {
-        "fma": 1 + y + (0 if int_chain else 2 * n_max),
-        "div": 0 if n_max <= 12 else 1,
-        "sqrt": 0,
-        "exp": 0,
-        "rsqrt": 1,
-    }
+    """FP64 operations of the asymptote row (Eq. "limf1"): F_0 = c_0 / sqrt(x),
+    y = 1/x and the upward chain F_m = F_{m-1} (m - 1/2) y.  The kernels form
+    F_0 and y by Newton steps for 1/sqrt(x) and run the chain, all on 64-bit
+    integer significands (csrc/boys_sig64.cuh), which leaves the FP64 pipe
+    nothing; int_chain=False counts the FP64 forms instead: a reciprocal
+    square root, F_0, y and two multiplications per order."""
+    if int_chain:
+        return dict(_NONE)
+    c = _asymptote_start_fp64(n_max)
+    c["fma"] += 2 * n_max
+    return c
 
 
 def int_chain_orders(n_max: int) -> int:
@@ -133,14 +142,14 @@ def f64_counts_contract(n_max: int, n_top: int, uniform: bool = True, int_chain:
     cut-off the row as f64_counts plus the n_max + 1 term dot product; above
     it, with the same coefficients for every argument and n_max <= 16, the
     contraction of the asymptote as a polynomial in y = 1/x (Horner, n_max
-    fused multiply-adds, y and two products), else the asymptote row and the
+    fused multiply-adds and the product with F_0, F_0 and y from the integer
+    start, or in FP64 with int_chain False), else the asymptote row and the
     dot product."""
     below, above = f64_counts(n_max, n_top, int_chain, rows=False)
     below["fma"] += n_max + 1
     if uniform and n_max <= 16:
-        # y = rs^2 (n_max <= 12) or 1/x, needed only from n_max = 1 on
-        above = {"fma": (1 if 1 <= n_max <= 12 else 0) + n_max + 2, "div": 1 if n_max > 12 else 0, "sqrt": 0,
-                 "exp": 0, "rsqrt": 1}
+        above = dict(_NONE) if int_chain else _asymptote_start_fp64(n_max)
+        above["fma"] += n_max + 1
     else:
         above = dict(above)
         above["fma"] += n_max + 1

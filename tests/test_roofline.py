@@ -67,30 +67,37 @@ def test_two_point_is_two_closed_forms_and_two_recursions():
 
 def test_contraction_counts():
     # below the cut-off: the row plus an (n_max + 1)-term dot product; above it
-    # with uniform weights: Horner in y = 1/x (y = rs^2 up to n_max = 12)
+    # with uniform weights: Horner in y = 1/x and the product with F_0, F_0 and
+    # y from the integer start (in FP64: a reciprocal square root, F_0, and y
+    # as rs^2 up to n_max = 12, else a division)
     for n_max, n_top in ((0, 0), (8, 9), (16, 18)):
         row_b, row_a = roofline.f64_counts(n_max, n_top)
         b, a = roofline.f64_counts_contract(n_max, n_top, uniform=True)
         assert b["fma"] == row_b["fma"] + n_max + 1 and b["exp"] == 1
-        assert a["fma"] == n_max + 2 + (1 if 1 <= n_max <= 12 else 0) and a["rsqrt"] == 1
-        # cheaper than the row and its dot product in FP64; with the row's chain
-        # on the integer pipes, no dearer than the row and its dot product
+        assert a["fma"] == n_max + 1 and a["rsqrt"] == 0 and a["div"] == 0
+        _, a64 = roofline.f64_counts_contract(n_max, n_top, uniform=True, int_chain=False)
+        assert a64["fma"] == n_max + 2 + (1 if 1 <= n_max <= 12 else 0) and a64["rsqrt"] == 1
+        assert a64["div"] == (1 if n_max > 12 else 0)
+        # cheaper than the row and its dot product in FP64; with the row on the
+        # integer pipes, no dearer than its dot product
         fp64_row = roofline.f64_counts(n_max, n_top, int_chain=False)[1]["fma"]
-        assert a["fma"] < fp64_row + n_max + 1 or n_max == 0
+        assert a64["fma"] < fp64_row + n_max + 1 or n_max == 0
         assert a["fma"] <= row_a["fma"] + n_max + 1
     b, a = roofline.f64_counts_contract(36, 40, uniform=True)  # no Horner above n_max = 16
     assert a["fma"] == roofline.f64_counts(36, 40)[1]["fma"] + 37
 
 
-def test_asymptote_chain_leaves_the_fp64_pipe():
-    # the upward chain's two multiplications per order run on the integer
-    # pipes; F_0 = c_0 rsqrt(x) and y = 1/x stay in FP64
+def test_asymptote_leaves_the_fp64_pipe():
+    # the upward chain's two multiplications per order, and F_0 = c_0 / sqrt(x)
+    # and y = 1/x (Newton steps for 1/sqrt(x)), run on the integer pipes; the
+    # all-FP64 form takes a reciprocal square root, F_0, y (rs^2 up to
+    # n_max = 12, else a division) and the chain
     for n_max in (0, 1, 8, 12, 13, 36):
         _, a = roofline.f64_counts(n_max, n_max)
         _, a64 = roofline.f64_counts(n_max, n_max, int_chain=False)
-        assert a64["fma"] - a["fma"] == 2 * n_max == 2 * roofline.int_chain_orders(n_max)
-        assert a["fma"] == 1 + (1 if 1 <= n_max <= 12 else 0) and a["rsqrt"] == 1
-        assert a["div"] == a64["div"] == (1 if n_max > 12 else 0)
+        assert a == {"fma": 0, "div": 0, "sqrt": 0, "exp": 0, "rsqrt": 0}
+        assert a64["fma"] == 1 + (1 if 1 <= n_max <= 12 else 0) + 2 * roofline.int_chain_orders(n_max)
+        assert a64["rsqrt"] == 1 and a64["div"] == (1 if n_max > 12 else 0)
 
 
 def test_integer_recursion_threshold_matches_the_kernels():

@@ -1,10 +1,10 @@
 """The integer significand arithmetic of the FP64 kernels' downward recursion
-and asymptote chain (csrc/boys_sig64.cuh), compiled for the host and checked
+and asymptote (csrc/boys_sig64.cuh), compiled for the host and checked
 against exact integer and rational arithmetic (the truncated 64 x 64 high
 product, the rounding of a significand to a double, the constants
-prod_{k<=m} (k - 1/2) and 1/(2m - 1), the bound below which every F_m of the
-chain is a normal double), and, composed as the kernels compose it, against
-the oracle."""
+prod_{k<=m} (k - 1/2), 1/(2m - 1) and sqrt(pi)/2, the reciprocal square root
+by Newton steps, the bound below which every F_m of the chain is a normal
+double), and, composed as the kernels compose it, against the oracle."""
 import math
 import os
 import shutil
@@ -52,6 +52,43 @@ int main() {
         const Sig64 k = recip_odd(2 * m - 1);
         sig64_mul(sf, ef, k.s, k.e);
         std::printf("%llu ", (unsigned long long)sig64_round_bits(sf, ef));
+      }
+      std::printf("\n");
+    } else if (op[0] == 'q') {  // q x_bits seed_bits: 1/sqrt(x) by sig64_rsqrt
+      unsigned long long xb;
+      unsigned sb;
+      std::scanf("%llu %u", &xb, &sb);
+      uint64_t s;
+      int es;
+      sig64_rsqrt(xb, sb, s, es);
+      std::printf("%llu %d\n", (unsigned long long)s, es);
+    } else if (op[0] == 'k') {  // k x_bits: sig64_rsqrt_reduce
+      unsigned long long xb;
+      std::scanf("%llu", &xb);
+      int k;
+      const uint32_t ab = sig64_rsqrt_reduce(xb, k);
+      std::printf("%u %d\n", ab, k);
+    } else if (op[0] == 'a') {  // a n x_bits seed_bits: F_0 .. F_n as the kernels' integer asymptote
+      unsigned long long xb;
+      unsigned sb;
+      std::scanf("%d %llu %u", &e, &xb, &sb);
+      uint64_t sr, sy, s;
+      int er, ey, es;
+      sig64_rsqrt(xb, sb, sr, er);
+      sy = sr;
+      ey = er;
+      sig64_mul(sy, ey, sr, er);  // y = r^2
+      s = kSig64C0s;
+      es = kSig64C0e;
+      sig64_mul(s, es, sr, er);  // F_0 = c_0 r
+      std::printf("%llu ", (unsigned long long)sig64_round_bits(s, es));
+      for (int m = 1; m <= e; ++m) {
+        sig64_mul(s, es, sy, ey);
+        const Sig64 h = half_odd_product(m);
+        uint64_t w = s;
+        int ew = es;
+        sig64_mul(w, ew, h.s, h.e);
+        std::printf("%llu ", (unsigned long long)sig64_round_bits(w, ew));
       }
       std::printf("\n");
     } else if (op[0] == 'c') {  // c n f0_bits y_bits: F_1 .. F_n by the integer chain
@@ -211,4 +248,77 @@ def test_integer_chain_against_the_oracle(run, oracle_mod, n):
     ref = oracle_mod.boys_ld(x, n)[:, 1:]
     rel = (np.abs(got - ref) / ref).astype(np.float64)
     bound = (3.5 + np.arange(1, n + 1)) * 2.0**-53
+    assert np.all(rel.max(axis=0) <= bound), (rel.max(axis=0) / 2.0**-53)
+
+
+def _float_bits(v):
+    return struct.unpack("<I", struct.pack("<f", v))[0]
+
+
+def _float(bits):
+    return struct.unpack("<f", struct.pack("<I", bits))[0]
+
+
+def _seeds(run, xs, rng, spread):
+    """The kernels' seed: x = a 4^k, a's leading bits as a float (checked
+    here), then a float approximation of 1/sqrt(a), here the nearest float
+    moved by up to `spread` relative (the device's rsqrtf is within 2^-22)."""
+    red = [line.split() for line in run([f"k {_bits(x)}" for x in xs])]
+    seeds = []
+    for x, (ab, k) in zip(xs, red):
+        a = _float(int(ab))
+        assert 1.0 <= a < 4.0 and abs(Fraction(a) * Fraction(4) ** int(k) / Fraction(float(x)) - 1) < Fraction(1, 2**23)
+        r0 = np.float32(1.0 / math.sqrt(a) * (1.0 + rng.uniform(-spread, spread)))
+        seeds.append(_float_bits(r0))
+    return seeds
+
+
+def test_reciprocal_square_root_by_newton_steps(run):
+    """sig64_rsqrt from seeds within 2^-20 of 1/sqrt(a): within 2^-60 of
+    1/sqrt(x) over the whole normal range, both exponent parities and the
+    seeds' power-of-two edges (r = 1 exactly at a = 1)."""
+    rng = np.random.default_rng(21)
+    xs = list(np.exp(rng.uniform(math.log(2.3e-308), math.log(1.7e308), 4000)))
+    xs += [1.0, 2.0, 4.0, 0.25, 0.5, 3.9999999999999996, 1.0000000000000002, 2.2250738585072014e-308,
+           1.7976931348623157e308, 7.0, 110.0, 1e8]
+    seeds = _seeds(run, xs, rng, 2.0**-20)
+    got = [tuple(int(t) for t in line.split()) for line in run([f"q {_bits(x)} {s}" for x, s in zip(xs, seeds)])]
+    for x, (s, e) in zip(xs, got):
+        assert 1 << 63 <= s < 1 << 64
+        r = Fraction(s) * Fraction(2) ** (e - 63)
+        # r^2 x = (1 + eps)^2: |eps| <= 2^-60 within |r^2 x - 1| <= 2^-59 + 2^-120
+        assert abs(r * r * Fraction(float(x)) - 1) <= Fraction(1, 2**59) + Fraction(1, 2**120), x
+
+
+def test_sqrt_pi_over_two_constant():
+    # the 64-bit significand of c_0 = sqrt(pi)/2 in csrc/boys_sig64.cuh is the
+    # nearest to 2^64 sqrt(pi)/2: its square times 4 brackets pi
+    import re
+
+    src = open(HEADER).read()
+    s = int(re.search(r"kSig64C0s = (0x[0-9a-f]+)ull", src).group(1), 16)
+    assert int(re.search(r"kSig64C0e = (-?\d+);", src).group(1)) == -1
+    pi_lo, pi_hi = Fraction(314159265358979323846264338327950288, 10**35), Fraction(314159265358979323846264338327950289, 10**35)
+    lo, hi = Fraction(s) - Fraction(1, 2), Fraction(s) + Fraction(1, 2)  # s 2^-64 within half a unit
+    assert 4 * (lo / 2**64) ** 2 < pi_lo and pi_hi < 4 * (hi / 2**64) ** 2
+
+
+@pytest.mark.parametrize("n", [0, 1, 8, 12, 16, 36])
+def test_integer_asymptote_against_the_oracle(run, oracle_mod, n):
+    """F_0 = c_0 / sqrt(x) and the chain, as the kernels form them above the
+    cut-off on the integer pipes (sig64_rsqrt from a seed within 2^-21, y = r^2,
+    F_0 = c_0 r, all to 64 bits): each F_m is one rounding (2^-53) from the
+    exact asymptote, whose distance from F_m is below 2^-53 above z_{n,53},
+    plus the 64-bit arithmetic (below m 2^-58): within 2 + m/32 units of 2^-53
+    of the oracle's long double value."""
+    rng = np.random.default_rng(200 + n)
+    xmax = _double(int(run([f"x {max(n, 1)}"])[0])) if n else 1e300
+    z = oracle_mod.cutoff(n, 53)
+    x = np.exp(rng.uniform(math.log(z), math.log(min(xmax, 1e300)) - 1e-9, 2000))
+    seeds = _seeds(run, list(x), rng, 2.0**-21)
+    lines = [f"a {n} {_bits(a)} {s}" for a, s in zip(x, seeds)]
+    got = np.array([[_double(int(t)) for t in line.split()] for line in run(lines)])  # F_0 .. F_n
+    ref = oracle_mod.boys_ld(x, n)
+    rel = (np.abs(got - ref) / ref).astype(np.float64)
+    bound = (2.0 + np.arange(0, n + 1) / 32.0) * 2.0**-53
     assert np.all(rel.max(axis=0) <= bound), (rel.max(axis=0) / 2.0**-53)
