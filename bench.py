@@ -786,6 +786,10 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
             int_rec = roofline.int_recursion(n_top, n_max)
         rec_note = ("and the downward recursion run on the integer pipes and are not counted" if int_rec else
                     "runs on the integer pipes and is not counted; the downward recursion stays in FP64")
+        if roofline.int_rsqrt(n_max, bool(wl.get("two_point"))):
+            rec_note += "; so do F_0 = c_0/sqrt(x), 1/x and the closed form's reciprocal square roots (Newton steps)"
+        else:
+            rec_note += "; so do F_0 = c_0/sqrt(x) and 1/x (Newton steps)"
         achieved = t_arg * rates["fma"] * count / (ms / 1e3) / 1e12
         achieved64 = t_per_arg(False) * rates["fma"] * count / (ms / 1e3) / 1e12
         peak = rates["fma"] / 1e12
@@ -798,7 +802,7 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
             "peak": round(peak, 5),
             "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4),
-            "traffic": None if wl.get("two_point") else traffic_record(f"f64_split_kernel<{n_max}>/scale_2^26"),
+            "traffic": None if wl.get("two_point") else traffic_record(f"f64_rows<{n_max}>/scale_2^26"),
             "note": "FP64-pipe instruction equivalents per second (1 per add/mul/fma; exp, sqrt, rsqrt and div "
             "weighted by their measured cost) vs the DFMA rate measured in this run; the asymptote's upward "
             f"product chain ({roofline.int_chain_orders(n_max)} orders) {rec_note}; "

@@ -83,14 +83,59 @@ __device__ __forceinline__ double exp_neg(double x, const double *__restrict__ t
   return __longlong_as_double(__double_as_longlong(res) + ((long long)(k >> 6) << 52));
 }
 
+// The float approximation that seeds the Newton steps: one special-function
+// instruction (relative error about 2^-23 on [1, 4)).
+__device__ __forceinline__ float rsqrt_approx_f32(float a) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+
+// 1/sqrt(v) for a positive normal double v as a Sig64 within 2^-60, by
+// Newton steps on the integer pipes (boys_sig64.cuh) from a float
+// approximation for v's leading bits.  In FP64 a reciprocal square root
+// costs about 5 FMA times on the FP64 pipe, which bounds most kernels; this
+// takes about 70 integer instructions.
+__device__ __forceinline__ void f64_rsqrt_sig(const double v, uint64_t &s, int &e) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  int k;
+  const uint32_t ab = sig64_rsqrt_reduce(b, k);
+  sig64_rsqrt(b, __float_as_uint(rsqrt_approx_f32(__uint_as_float(ab))), s, e);
+}
+// nonzero, finite and not subnormal
+__device__ __forceinline__ bool f64_is_normal(const double v) {
+  return ((((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff) - 1ull) < 2046ull;
+}
+// the double nearest s 2^(e - 63) (positive), if it is normal
+__device__ __forceinline__ bool sig64_to_double(const uint64_t s, const int e, double &v) {
+  v = __longlong_as_double((long long)sig64_round_bits(s, e));
+  return (unsigned)(e + 1022) <= 2045u;
+}
+
 // Below the cut-off z_{NTOP,53} (Sec. 2): with s = NTOP + 1/2,
 //   Q   = q0 + q1 x + q2 x^2 u(x)/v(x)      (Eq. "pqz"; u, v root products, Eqs. "pz"/"qz")
 //   D   = x + Q^NTOP sqrt(Q) e^{-x}          (Eq. "fq")
 //   F_NTOP = c_NTOP D^{-s}
 //   F_{m-1} = (2x F_m + e^{-x}) / (2m-1)     (Eq. "r", same e^{-x}; the printed
 //                                             denominator 2m+1 is read as 2m-1)
-// F_NTOP(x) by the closed form of Eq. "fq", given e = e^{-x}.
-template <int NTOP>
+// Whether the closed form takes its reciprocal square roots from integer
+// Newton steps (f64_rsqrt_sig): below n_max = 12 and in the two-point rows,
+// whose kernels the FP64 pipe bounds.  The one-point rows from n_max = 12 on
+// are bound by issue and latency instead, and the extra integer work cost
+// them 1-4% (n_max = 16: 232.0 -> 229.6, 36: 280.4 -> 270.2 G values/s),
+// against +21% at n_max = 4 (102.6 -> 123.7), +11.5% for the staged rows of
+// n_max = 8 (155.0 -> 172.9) and two-point n_max = 36 (187.4 -> 209.0).  The
+// rule depends on the order only, so rows, contractions, gradients and ragged
+// requests of one order share their arithmetic bit for bit.
+__host__ __device__ constexpr bool f64_int_rsqrt(int n_max, bool two) { return two || n_max < 12; }
+
+// F_NTOP(x) by the closed form of Eq. "fq", given e = e^{-x}.  INT: sqrt(Q) =
+// Q rsqrt(Q), r = D^{-1/2} and w = r^2 from the integer Newton steps above,
+// each rounded once to a double, and D^{-s} = r w^NTOP (the FP64 forms
+// remain for operands outside the normal range).  Otherwise in FP64:
+// rsqrt(D)^{2 NTOP + 1} up to n_top = 13, else (1/D)^NTOP sqrt(1/D).  u/v is
+// an FP64 division either way (the integer reciprocal measured no faster).
+template <int NTOP, bool INT>
 __device__ __forceinline__ double f64_closed_form(const double x, const double e) {
   using Tab = BoysF64<NTOP>;
   double u, v;
@@ -98,14 +143,49 @@ __device__ __forceinline__ double f64_closed_form(const double x, const double e
   const double r = u / v;
   const double p = (Tab::kQ2 * x) * x;
   const double q = fma(p, r, fma(Tab::kQ1, x, Tab::kQ0));
-  const double T = (ipow<NTOP>(q) * (q * rsqrt(q))) * e;
-  const double D = x + T;
-  if constexpr (NTOP <= 13) {
-    const double rs = rsqrt(D);  // D^{-s} = rs^{2 NTOP + 1}
-    return (Tab::kC * rs) * ipow<NTOP>(rs * rs);
+  if constexpr (!INT) {
+    const double T = (ipow<NTOP>(q) * (q * rsqrt(q))) * e;
+    const double D = x + T;
+    if constexpr (NTOP <= 13) {
+      const double rs = rsqrt(D);  // D^{-s} = rs^{2 NTOP + 1}
+      return (Tab::kC * rs) * ipow<NTOP>(rs * rs);
+    } else {
+      const double w = 1.0 / D;  // D^{-s} = w^NTOP sqrt(w)
+      return (Tab::kC * ipow<NTOP>(w)) * (w * rsqrt(w));
+    }
   } else {
-    const double w = 1.0 / D;  // D^{-s} = w^NTOP sqrt(w)
-    return (Tab::kC * ipow<NTOP>(w)) * (w * rsqrt(w));
+    double sq;  // sqrt(q)
+    {
+      uint64_t sr, sqs = sig64_of_bits((uint64_t)__double_as_longlong(q));
+      int er, eq = exp_of_bits((uint64_t)__double_as_longlong(q));
+      bool ok = q > 0.0 && f64_is_normal(q);
+      if (ok) {
+        f64_rsqrt_sig(q, sr, er);
+        sig64_mul(sqs, eq, sr, er);
+        ok = sig64_to_double(sqs, eq, sq);
+      }
+      if (!ok) sq = q * rsqrt(q);
+    }
+    const double T = (ipow<NTOP>(q) * sq) * e;
+    const double D = x + T;
+    double rs, w;  // D^{-1/2} and 1/D
+    {
+      uint64_t sr, sw;
+      int er, ew;
+      bool ok = f64_is_normal(D);
+      if (ok) {
+        f64_rsqrt_sig(D, sr, er);
+        sw = sr;
+        ew = er;
+        sig64_mul(sw, ew, sr, er);
+        ok = sig64_to_double(sr, er, rs) && sig64_to_double(sw, ew, w);
+      }
+      if (!ok) {
+        rs = rsqrt(D);
+        w = 1.0 / D;
+      }
+    }
+    return (Tab::kC * rs) * ipow<NTOP>(w);  // D^{-s} = rs w^NTOP
   }
 }
 
@@ -206,7 +286,7 @@ __device__ __forceinline__ void f64_recurse(double f, const double tx, const dou
 template <int NTOP, int NMAX>
 __device__ __forceinline__ void f64_formula(const double x, double (&F)[NMAX + 1], const double *__restrict__ tab64) {
   const double e = exp_neg(x, tab64);
-  f64_recurse<NTOP, 0, NMAX>(f64_closed_form<NTOP>(x, e), twice(x), e, F);
+  f64_recurse<NTOP, 0, NMAX>(f64_closed_form<NTOP, f64_int_rsqrt(NMAX, false)>(x, e), twice(x), e, F);
 }
 
 // Order n_bar of the two-point evaluation: the lower half of the orders.
@@ -223,9 +303,9 @@ __device__ __forceinline__ void f64_formula_two(const double x, double (&F)[NMAX
   constexpr bool INT = f64_int_recursion(NTOP - NBAR - 1 + NTOP_LO);
   const double e = exp_neg(x, tab64);
   const double tx = twice(x);
-  f64_recurse<NTOP, NBAR + 1, NMAX, INT>(f64_closed_form<NTOP>(x, e), tx, e, F);
+  f64_recurse<NTOP, NBAR + 1, NMAX, INT>(f64_closed_form<NTOP, true>(x, e), tx, e, F);
   double lo[NBAR + 1];
-  f64_recurse<NTOP_LO, 0, NBAR, INT>(f64_closed_form<NTOP_LO>(x, e), tx, e, lo);
+  f64_recurse<NTOP_LO, 0, NBAR, INT>(f64_closed_form<NTOP_LO, true>(x, e), tx, e, lo);
 #pragma unroll
   for (int m = 0; m <= NBAR; ++m) F[m] = lo[m];
 }
@@ -264,12 +344,9 @@ __device__ __forceinline__ bool sig64_chain_ok(const double x) {
 // the high orders' y, a division: about 5 and 7.6 FMA times on the FP64
 // pipe, which bounds the kernels.
 __device__ __forceinline__ double f64_asymptote_start(const double x, uint64_t &sf, int &ef, uint64_t &sy, int &ey) {
-  const uint64_t xb = (uint64_t)__double_as_longlong(x);
-  int k;
-  const uint32_t ab = sig64_rsqrt_reduce(xb, k);
   uint64_t sr;
   int er;
-  sig64_rsqrt(xb, __float_as_uint(rsqrtf(__uint_as_float(ab))), sr, er);
+  f64_rsqrt_sig(x, sr, er);
   sy = sr;
   ey = er;
   sig64_mul(sy, ey, sr, er);
@@ -501,7 +578,7 @@ __device__ __forceinline__ void f64_formula_staged(const double (&x)[K], const i
   for (int k = 0; k < K; ++k) {
     e[k] = exp_neg(x[k], tab64);
     tx[k] = twice(x[k]);
-    f[k] = f64_closed_form<NTOP>(x[k], e[k]);
+    f[k] = f64_closed_form<NTOP, f64_int_rsqrt(NMAX, TWO)>(x[k], e[k]);
   }
   if constexpr (!TWO) {
     f64_recurse_staged<NTOP, 0, NMAX, W, CH, K, true>(f, tx, e, j, out, stg, lane);
@@ -515,7 +592,7 @@ __device__ __forceinline__ void f64_formula_staged(const double (&x)[K], const i
     constexpr bool INT = f64_int_recursion(NTOP - NBAR - 1 + NTOP_LO);
     f64_recurse_staged<NTOP, NBAR + 1, NMAX, W, CH, K, INT>(f, tx, e, j, out, stg, lane);
 #pragma unroll
-    for (int k = 0; k < K; ++k) f[k] = f64_closed_form<NTOP_LO>(x[k], e[k]);
+    for (int k = 0; k < K; ++k) f[k] = f64_closed_form<NTOP_LO, true>(x[k], e[k]);
     f64_recurse_staged<NTOP_LO, 0, NBAR, W, CH, K, INT>(f, tx, e, j, out, stg, lane);
   }
 }
@@ -1023,7 +1100,8 @@ constexpr size_t f64_stage_bytes() {
 }
 
 // Resident blocks per SM that a staged kernel is compiled for: as many as its
-// shared memory allows (228 KB per SM, 1 KB reserved per block), at most 4;
+// shared memory allows (228 KB per SM, 1 KB reserved per block), at most 4
+// (6 for the whole-row staging of n_max = 8 to 11);
 // the register budget follows from it.  Blocks of 256 threads with 2048-
 // argument tiles take 55.4 KB: 4 blocks of 64 registers.  Against 3 blocks
 // of 80 registers with odd-pitch rows (57.4 KB), n_max = 20 / 24 / 28 / 32 /
@@ -1036,7 +1114,11 @@ constexpr int f64_min_blocks() {
   if (STAGE == 0) return 1;
   const size_t per_block = sizeof(F64TileSmem<TILE, true>) + f64_stage_bytes<BLOCK, STAGE, K>() + 1024;
   const int b = (int)((size_t)228 * 1024 / per_block);
-  return b < 1 ? 1 : (b > 4 ? 4 : b);
+  // the whole-row staging below n_max = 12 (1024-argument tiles, 31.7 KB)
+  // runs 6 blocks of 40 registers (7 of 32 spilled; n_max = 8: 177.1
+  // against 170.9 G values/s)
+  const int cap = (BLOCK == 256 && STAGE < 16) ? 6 : 4;
+  return b < 1 ? 1 : (b > cap ? cap : b);
 }
 
 // Tiles of a persistent block (all kernels below).
@@ -1178,11 +1260,11 @@ int launch_f64_shape(const double *x, int64_t count, const MakeEpi &epi, cudaStr
   }
 }
 
-template <int NMAX, typename MakeEpi, bool TWO = false, int STAGE = 0, int K = 2>
+template <int NMAX, typename MakeEpi, bool TWO = false, int STAGE = 0, int K = 2, int TILE = kF64Tile>
 int launch_f64_epi(const double *x, int64_t count, const MakeEpi &epi, cudaStream_t s) {
   if (count <= kF64SmallCount)
     return launch_f64_shape<NMAX, kF64SmallBlock, kF64SmallTile, MakeEpi, TWO, STAGE, K>(x, count, epi, s);
-  return launch_f64_shape<NMAX, kF64Block, kF64Tile, MakeEpi, TWO, STAGE, K>(x, count, epi, s);
+  return launch_f64_shape<NMAX, kF64Block, TILE, MakeEpi, TWO, STAGE, K>(x, count, epi, s);
 }
 
 // Row staging from n_max = 12 on: orders per flush of the staging buffer
@@ -1197,11 +1279,25 @@ int launch_f64_epi(const double *x, int64_t count, const MakeEpi &epi, cudaStrea
 // the same way: n_max = 36 173.7 -> 175.8.
 constexpr int kF64StageOrders = 16, kF64StageK = 1;
 constexpr int kF64TwoStageOrders = 16, kF64TwoStageK = 1;
+// From n_max = 8 to 11 the whole row is staged (one flush of n_max + 1
+// orders) in 1024-argument tiles: once the asymptote and the closed form's
+// reciprocal square roots left the FP64 pipe, the rows stored from the
+// lanes' registers (a store instruction writes 8 bytes into each of 32
+// sectors) held n_max = 8 at 136.2 G values/s, against 177.1 staged; n_max =
+// 9 / 10 / 11 132.8 / 144.2 / 183.0 -> 189.4 / 195.2 / 199.8.  Below n_max = 8
+// the lanes' stores stay faster (n_max = 7: 177.4 against 164.6; 4: 123.8
+// against 118.3).
+constexpr int kF64RowStageFrom = 8, kF64RowStageTile = 1024;
+__host__ __device__ constexpr int f64_row_stage(int n_max) {
+  return n_max >= 12 ? kF64StageOrders : (n_max >= kF64RowStageFrom ? n_max + 1 : 0);
+}
 
 template <int NMAX>
 int launch_f64(const double *x, int64_t count, double *out, cudaStream_t s) {
-  return launch_f64_epi<NMAX, MakeStore<NMAX + 1>, false, (NMAX >= 12 ? kF64StageOrders : 0), kF64StageK>(
-      x, count, MakeStore<NMAX + 1>{out}, s);
+  constexpr int STAGE = f64_row_stage(NMAX);
+  constexpr int TILE = (STAGE > 0 && NMAX < 12) ? kF64RowStageTile : kF64Tile;
+  return launch_f64_epi<NMAX, MakeStore<NMAX + 1>, false, STAGE, kF64StageK, TILE>(x, count,
+                                                                                   MakeStore<NMAX + 1>{out}, s);
 }
 
 // Backward with the forward rows recomputed: the order n_max + 1 is needed.

@@ -89,6 +89,19 @@ BOYS_HD uint64_t sig64_round_bits(uint64_t s, int e) {
   return m + ((uint64_t)(e + 1022) << 52);
 }
 
+// r + c (d >= 0) or r - c (d < 0) for a correction c below r 2^-18, renormalised
+// (a carry out of the 64 bits, or a fall below 2^63, moves the exponent by
+// one).  Selects, not branches: the sign of d differs from lane to lane.
+BOYS_HD void sig64_nudge(uint64_t &s, int &e, int64_t d, uint64_t c) {
+  const uint64_t up = s + c, dn = s - c;
+  const bool pos = d >= 0;
+  const bool carry = pos && up < s;
+  const bool borrow = !pos && dn < (1ull << 63);
+  const uint64_t u = pos ? up : dn;
+  s = carry ? (u >> 1) | (1ull << 63) : (borrow ? u << 1 : u);
+  e += (int)carry - (int)borrow;
+}
+
 // 1/sqrt(x) for a positive normal double x, by Newton's method on 64-bit
 // significands.  Write x = a 4^k with a in [1, 4).  sig64_rsqrt_reduce gives
 // k and the bits of a float holding a's leading 24 bits, whose reciprocal
@@ -120,24 +133,7 @@ BOYS_HD void sig64_rsqrt(uint64_t xbits, uint32_t seed_bits, uint64_t &s, int &e
     sig64_mul(t, et, sa, p);
     // d 2^64 from t 2^(et - 63), et being -1 (t < 1) or 0 (t >= 1)
     const int64_t d = et == 0 ? -(int64_t)((t - (1ull << 63)) << 1) : (int64_t)(0ull - t);
-    const uint64_t c = mulhi_trunc(sr, d < 0 ? (uint64_t)(-d) : (uint64_t)d) >> 1;  // r |d| / 2
-    if (d >= 0) {
-      const uint64_t u = sr + c;
-      if (u < sr) {  // carried out: r crossed a power of two upwards
-        sr = (u >> 1) | (1ull << 63);
-        er += 1;
-      } else {
-        sr = u;
-      }
-    } else {
-      const uint64_t u = sr - c;
-      if (u < (1ull << 63)) {  // r crossed a power of two downwards
-        sr = u << 1;
-        er -= 1;
-      } else {
-        sr = u;
-      }
-    }
+    sig64_nudge(sr, er, d, mulhi_trunc(sr, d < 0 ? (uint64_t)(-d) : (uint64_t)d) >> 1);  // r |d| / 2
   }
   s = sr;
   e = er - k;

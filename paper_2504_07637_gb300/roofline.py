@@ -4,9 +4,12 @@ Counts follow the method (Sec. 2) as the double kernels evaluate it: below the
 cut-off one evaluation of Q~ in root-product form, one division u/v, one
 exponential (shared with the recursion, Eq. "r"), the half-integer powers
 Q^{n+1/2} and D^{-(n+1/2)} as square-and-multiply plus a reciprocal square
-root each, and two operations per step of the downward recursion (on the
-integer pipes instead in the row kernels, and for recursions of up to 18
-steps elsewhere); above it (Eq. "limf1") nothing on the FP64 pipe: F_0 and
+root each (below n_max = 12 and in the two-point rows the kernels take the
+reciprocal square roots from Newton steps on 64-bit integer significands),
+and two operations per step of
+the downward recursion (on the integer pipes instead in the row kernels, and
+for recursions of up to 18 steps elsewhere); above it (Eq. "limf1") nothing
+on the FP64 pipe: F_0 and
 1/x come from a reciprocal square root by Newton steps on 64-bit integer
 significands, and the upward product chain runs there too.  The all-FP64
 form (int_chain=False) counts one reciprocal square root, F_0, 1/x and the
@@ -44,13 +47,31 @@ def square_multiply_ops(k: int) -> int:
     return (k.bit_length() - 1) + (bin(k).count("1") - 1)
 
 
-def _closed_form_counts(n_top: int) -> dict:
-    """Operations of F_{n_top} by the closed form (Eq. "fq") given e^{-x}:
-    Q~ in root-product form and one division u/v, Q^n and Q rsqrt(Q), D, and
-    D^{-s} as rsqrt(D)^{2n+1} for n_top <= 13, else (1/D)^n (1/D) rsqrt(1/D)."""
+def int_rsqrt(n_max: int, two_point: bool = False) -> bool:
+    """Whether the closed form takes its reciprocal square roots from integer
+    Newton steps (f64_int_rsqrt in csrc/boys_f64.cuh): below n_max = 12 and
+    in the two-point rows."""
+    return two_point or n_max < INT_RSQRT_BELOW
+
+
+INT_RSQRT_BELOW = 12
+
+
+def _closed_form_counts(n_top: int, int_newton: bool = True) -> dict:
+    """FP64 operations of F_{n_top} by the closed form (Eq. "fq") given
+    e^{-x}: Q~ in root-product form with one division u/v, Q^n, sqrt(Q), D
+    and D^{-s}.  int_newton: sqrt(Q) = Q rsqrt(Q), r = D^{-1/2} and w = r^2
+    from Newton steps on 64-bit integer significands, D^{-s} = r w^n, so the
+    FP64 pipe keeps Q~, the division, the powers and four products.  In FP64
+    (int_newton False): Q rsqrt(Q), and rsqrt(D)^{2n+1} for n_top <= 13,
+    else (1/D)^n (1/D) rsqrt(1/D)."""
     rec = _fits(53)[n_top]
     pw = square_multiply_ops(n_top)
-    fma = root_product_ops(rec["u"]) + root_product_ops(rec["v"]) + 4  # Q~
+    fma = root_product_ops(rec["u"]) + root_product_ops(rec["v"]) + 4  # Q~ (given u/v)
+    if int_newton:
+        fma += pw + 1 + 1 + 1  # Q^n, times sqrt(Q), times e^{-x}, plus x
+        fma += pw + 2  # w^n, c r and the product
+        return {"fma": fma, "div": 1, "sqrt": 0, "exp": 0, "rsqrt": 0}
     fma += pw + 1 + 1 + 1 + 1  # Q^n, Q rsqrt(Q), product, times e^{-x}, plus x
     if n_top <= 13:
         fma += 1 + pw + 2  # rs^2, its power, c rs and the product
@@ -114,7 +135,7 @@ def f64_counts(n_max: int, n_top: int, int_chain: bool = True, rows: bool = True
     it.  rows: the row kernel (else an unstaged epilogue kernel).  With
     int_chain False, the recursion and the asymptote's chain are both
     counted in FP64 (the all-FP64 kernel)."""
-    below = _closed_form_counts(n_top)
+    below = _closed_form_counts(n_top, int_chain and int_rsqrt(n_max))
     below["exp"] = 1
     if not (int_chain and int_recursion(n_top, n_max if rows else None)):
         below["fma"] += 2 * n_top  # recursion
@@ -126,8 +147,8 @@ def f64_counts_two_point(n_max: int, n_top: int, n_bar: int, n_top_lo: int,
     """As f64_counts for the two-point evaluation (Trick B of Sec. 3): closed
     forms at n_top and at n_top_lo sharing one exponential, the recursion
     from n_top down to n_bar + 1 and the one from n_top_lo down to 0."""
-    below = _closed_form_counts(n_top)
-    lo = _closed_form_counts(n_top_lo)
+    below = _closed_form_counts(n_top, int_chain)
+    lo = _closed_form_counts(n_top_lo, int_chain)
     for k in below:
         below[k] += lo[k]
     below["exp"] = 1

@@ -113,7 +113,34 @@ def test_integer_recursion_threshold_matches_the_kernels():
     for n_max, n_top in ((8, 9), (16, 18), (17, 19), (36, 40)):
         b, _ = roofline.f64_counts(n_max, n_top)
         b64, _ = roofline.f64_counts(n_max, n_top, int_chain=False)
-        assert b64["fma"] - b["fma"] == 2 * n_top
+        # the closed form's own difference below n_max = 12: rsqrt(Q) and
+        # D^{-1/2} as integer Newton steps
+        cf = roofline._closed_form_counts(n_top, False)["fma"] - roofline._closed_form_counts(n_top, True)["fma"]
+        cf = cf if roofline.int_rsqrt(n_max) else 0
+        assert b64["fma"] - b["fma"] == 2 * n_top + cf
         e, _ = roofline.f64_counts(n_max, n_top, rows=False)
-        assert b64["fma"] - e["fma"] == (2 * n_top if n_top <= 18 else 0)
+        assert b64["fma"] - e["fma"] == cf + (2 * n_top if n_top <= 18 else 0)
     assert "f64_recurse_staged<NTOP, 0, NMAX, W, CH, K, true>" in src
+
+
+def test_closed_form_newton_steps_leave_the_fp64_pipe():
+    # Q rsqrt(Q) and D^{-1/2} (with its square) as integer Newton steps below
+    # n_max = 12 and in the two-point rows: no FP64 reciprocal square root is
+    # left, the division u/v stays; the FP64 form differs by exactly those and
+    # the products they replace
+    for n_top in (1, 9, 13, 14, 18, 40):
+        c = roofline._closed_form_counts(n_top)
+        c64 = roofline._closed_form_counts(n_top, False)
+        assert c["rsqrt"] == 0 and c["div"] == 1
+        assert c64["rsqrt"] == 2 and c64["div"] == (1 if n_top <= 13 else 2)
+        assert c64["fma"] - c["fma"] == 2  # Q rsqrt(Q), and rs^2 or w rsqrt(w)
+    import re
+
+    src = open(os.path.join(os.path.dirname(roofline.__file__), "csrc", "boys_f64.cuh")).read()
+    m = re.search(r"constexpr bool f64_int_rsqrt\(int n_max, bool two\) \{ return two \|\| n_max < (\d+); \}", src)
+    assert m and int(m.group(1)) == roofline.INT_RSQRT_BELOW
+    for n_max, n_top in ((8, 9), (11, 12), (12, 13), (16, 18)):
+        b, _ = roofline.f64_counts(n_max, n_top)
+        assert b["rsqrt"] == (0 if n_max < 12 else 2)
+        two, _ = roofline.f64_counts_two_point(n_max, n_top, n_max // 2, n_max // 2 + 1)
+        assert two["rsqrt"] == 0
