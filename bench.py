@@ -669,7 +669,10 @@ def run_grad(args, wl, emit=True):
     q1.record(stream)
     q1.synchronize()
     bwd_queued_ms = q0.elapsed_time(q1) / 20
-    # the backward without saved rows (recomputed in the kernel), device time
+    # the backward without saved rows (recomputed in the kernel), device time;
+    # one untimed call first (the kernel's first launch loads and sets it up)
+    boys.boys_backward(xd, gw, n_max, None)
+    torch.cuda.synchronize()
     q0.record(stream)
     for _ in range(5):
         boys.boys_backward(xd, gw, n_max, None)
