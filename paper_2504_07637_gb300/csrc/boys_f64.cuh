@@ -129,12 +129,30 @@ __device__ __forceinline__ bool sig64_to_double(const uint64_t s, const int e, d
 // requests of one order share their arithmetic bit for bit.
 __host__ __device__ constexpr bool f64_int_rsqrt(int n_max, bool two) { return two || n_max < 12; }
 
-// F_NTOP(x) by the closed form of Eq. "fq", given e = e^{-x}.  INT: sqrt(Q) =
-// Q rsqrt(Q), r = D^{-1/2} and w = r^2 from the integer Newton steps above,
-// each rounded once to a double, and D^{-s} = r w^NTOP (the FP64 forms
-// remain for operands outside the normal range).  Otherwise in FP64:
-// rsqrt(D)^{2 NTOP + 1} up to n_top = 13, else (1/D)^NTOP sqrt(1/D).  u/v is
-// an FP64 division either way (the integer reciprocal measured no faster).
+// F_NTOP(x) by the closed form of Eq. "fq", given e = e^{-x}.  Q~ (the root
+// products and u/v) and e^{-x} are FP64 either way.  INT: everything after
+// Q on 64-bit significands, rounded once at the end: T = Q^NTOP Q r_Q e^{-x}
+// with r_Q = 1/sqrt(Q), D = x + T, r_D = 1/sqrt(D) (integer Newton steps,
+// f64_rsqrt_sig), and F = c r_D (r_D^2)^NTOP; all terms are positive, and the
+// significands' exponents are plain integers, so neither Q^NTOP nor D^-NTOP
+// can leave a range.  Otherwise in FP64: rsqrt(D)^{2 NTOP + 1} up to
+// n_top = 13, else (1/D)^NTOP sqrt(1/D) (also the fallback for operands
+// outside the normal range).  An integer reciprocal for u/v measured no
+// faster than the FP64 division.
+template <int NTOP>
+__device__ __forceinline__ double f64_closed_form_tail_fp64(const double x, const double q, const double e) {
+  using Tab = BoysF64<NTOP>;
+  const double T = (ipow<NTOP>(q) * (q * rsqrt(q))) * e;
+  const double D = x + T;
+  if constexpr (NTOP <= 13) {
+    const double rs = rsqrt(D);  // D^{-s} = rs^{2 NTOP + 1}
+    return (Tab::kC * rs) * ipow<NTOP>(rs * rs);
+  } else {
+    const double w = 1.0 / D;  // D^{-s} = w^NTOP sqrt(w)
+    return (Tab::kC * ipow<NTOP>(w)) * (w * rsqrt(w));
+  }
+}
+
 template <int NTOP, bool INT>
 __device__ __forceinline__ double f64_closed_form(const double x, const double e) {
   using Tab = BoysF64<NTOP>;
@@ -143,50 +161,38 @@ __device__ __forceinline__ double f64_closed_form(const double x, const double e
   const double r = u / v;
   const double p = (Tab::kQ2 * x) * x;
   const double q = fma(p, r, fma(Tab::kQ1, x, Tab::kQ0));
-  if constexpr (!INT) {
-    const double T = (ipow<NTOP>(q) * (q * rsqrt(q))) * e;
-    const double D = x + T;
-    if constexpr (NTOP <= 13) {
-      const double rs = rsqrt(D);  // D^{-s} = rs^{2 NTOP + 1}
-      return (Tab::kC * rs) * ipow<NTOP>(rs * rs);
-    } else {
-      const double w = 1.0 / D;  // D^{-s} = w^NTOP sqrt(w)
-      return (Tab::kC * ipow<NTOP>(w)) * (w * rsqrt(w));
-    }
-  } else {
-    double sq;  // sqrt(q)
-    {
-      uint64_t sr, sqs = sig64_of_bits((uint64_t)__double_as_longlong(q));
-      int er, eq = exp_of_bits((uint64_t)__double_as_longlong(q));
-      bool ok = q > 0.0 && f64_is_normal(q);
-      if (ok) {
-        f64_rsqrt_sig(q, sr, er);
-        sig64_mul(sqs, eq, sr, er);
-        ok = sig64_to_double(sqs, eq, sq);
+  if constexpr (INT) {
+    if (q > 0.0 && f64_is_normal(q) && f64_is_normal(e)) {
+      const uint64_t qb = (uint64_t)__double_as_longlong(q), ebits = (uint64_t)__double_as_longlong(e);
+      const uint64_t sq = sig64_of_bits(qb);
+      const int eq = exp_of_bits(qb);
+      uint64_t sr, st = sq;
+      int er, et = eq;
+      f64_rsqrt_sig(q, sr, er);  // r_Q
+      sig64_pow<NTOP>(st, et);   // Q^NTOP
+      sig64_mul(st, et, sq, eq);
+      sig64_mul(st, et, sr, er);  // Q^(NTOP + 1/2)
+      sig64_mul(st, et, sig64_of_bits(ebits), exp_of_bits(ebits));
+      if (f64_is_normal(x)) {  // D = x + T (x >= 0; zero and subnormal x add nothing)
+        const uint64_t xb = (uint64_t)__double_as_longlong(x);
+        sig64_add(st, et, sig64_of_bits(xb), exp_of_bits(xb));
       }
-      if (!ok) sq = q * rsqrt(q);
+      uint64_t sd, sw;
+      int ed, ew;
+      sig64_rsqrt_sig(st, et, __float_as_uint(rsqrt_approx_f32(__uint_as_float(sig64_rsqrt_seed_arg(st, et)))), sd,
+                      ed);  // r_D
+      sw = sd;
+      ew = ed;
+      sig64_mul(sw, ew, sd, ed);  // w = 1/D
+      sig64_pow<NTOP>(sw, ew);
+      sig64_mul(sw, ew, sd, ed);  // D^{-s}
+      const uint64_t cb = (uint64_t)__double_as_longlong(Tab::kC);
+      sig64_mul(sw, ew, sig64_of_bits(cb), exp_of_bits(cb));
+      double F;
+      if (sig64_to_double(sw, ew, F)) return F;
     }
-    const double T = (ipow<NTOP>(q) * sq) * e;
-    const double D = x + T;
-    double rs, w;  // D^{-1/2} and 1/D
-    {
-      uint64_t sr, sw;
-      int er, ew;
-      bool ok = f64_is_normal(D);
-      if (ok) {
-        f64_rsqrt_sig(D, sr, er);
-        sw = sr;
-        ew = er;
-        sig64_mul(sw, ew, sr, er);
-        ok = sig64_to_double(sr, er, rs) && sig64_to_double(sw, ew, w);
-      }
-      if (!ok) {
-        rs = rsqrt(D);
-        w = 1.0 / D;
-      }
-    }
-    return (Tab::kC * rs) * ipow<NTOP>(w);  // D^{-s} = rs w^NTOP
   }
+  return f64_closed_form_tail_fp64<NTOP>(x, q, e);
 }
 
 // Constants of the integer loops that run over orders at run time, indexed

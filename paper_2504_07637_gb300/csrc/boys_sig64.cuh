@@ -119,11 +119,17 @@ BOYS_HD uint32_t sig64_rsqrt_reduce(uint64_t xbits, int &k) {
   return ((uint32_t)(127 + p) << 23) | (uint32_t)((xbits >> 29) & 0x7fffffu);
 }
 
-BOYS_HD void sig64_rsqrt(uint64_t xbits, uint32_t seed_bits, uint64_t &s, int &e) {
-  const int ex = exp_of_bits(xbits);
-  const int p = ex & 1;
-  const int k = (ex - p) / 2;
-  const uint64_t sa = sig64_of_bits(xbits);  // a = sa 2^(p - 63)
+// The seed's argument for a Sig64 value s 2^(e - 63): a float holding the
+// leading 24 bits of a = s 2^(p - 63) in [1, 4), p = e mod 2.
+BOYS_HD uint32_t sig64_rsqrt_seed_arg(uint64_t s, int e) {
+  return ((uint32_t)(127 + (e & 1)) << 23) | (uint32_t)((s >> 40) & 0x7fffffu);
+}
+
+// 1/sqrt of the positive number sa 2^(ea - 63), sa in [2^63, 2^64), from a
+// seed within 2^-20 of 1/sqrt(a) (a as in sig64_rsqrt_seed_arg).
+BOYS_HD void sig64_rsqrt_sig(uint64_t sa, int ea, uint32_t seed_bits, uint64_t &s, int &e) {
+  const int p = ea & 1;  // ea = 2k + p, also for negative ea (two's complement)
+  const int k = (ea - p) / 2;
   uint64_t sr = (uint64_t)((seed_bits & 0x7fffffu) | 0x800000u) << 40;
   int er = (int)((seed_bits >> 23) & 0xffu) - 127;
   for (int it = 0; it < 2; ++it) {
@@ -137,6 +143,29 @@ BOYS_HD void sig64_rsqrt(uint64_t xbits, uint32_t seed_bits, uint64_t &s, int &e
   }
   s = sr;
   e = er - k;
+}
+
+// The same for a positive normal double x.
+BOYS_HD void sig64_rsqrt(uint64_t xbits, uint32_t seed_bits, uint64_t &s, int &e) {
+  sig64_rsqrt_sig(sig64_of_bits(xbits), exp_of_bits(xbits), seed_bits, s, e);
+}
+
+// x^n (n >= 0) by repeated squaring, each product a sig64_mul.
+template <int N>
+BOYS_HD void sig64_pow(uint64_t &s, int &e) {
+  static_assert(N >= 0, "power");
+  if constexpr (N == 0) {
+    s = 1ull << 63;
+    e = 0;
+  } else if constexpr (N > 1) {
+    uint64_t bs = s;
+    int be = e;
+    sig64_pow<N / 2>(bs, be);
+    sig64_mul(bs, be, bs, be);
+    if constexpr (N % 2 == 1) sig64_mul(bs, be, s, e);
+    s = bs;
+    e = be;
+  }
 }
 
 // c_0 = sqrt(pi)/2 (Eq. "limf1": F_0 = c_0 / sqrt(x) above the cut-off),

@@ -60,17 +60,15 @@ INT_RSQRT_BELOW = 12
 def _closed_form_counts(n_top: int, int_newton: bool = True) -> dict:
     """FP64 operations of F_{n_top} by the closed form (Eq. "fq") given
     e^{-x}: Q~ in root-product form with one division u/v, Q^n, sqrt(Q), D
-    and D^{-s}.  int_newton: sqrt(Q) = Q rsqrt(Q), r = D^{-1/2} and w = r^2
-    from Newton steps on 64-bit integer significands, D^{-s} = r w^n, so the
-    FP64 pipe keeps Q~, the division, the powers and four products.  In FP64
-    (int_newton False): Q rsqrt(Q), and rsqrt(D)^{2n+1} for n_top <= 13,
-    else (1/D)^n (1/D) rsqrt(1/D)."""
+    and D^{-s}.  int_newton: everything after Q on 64-bit integer
+    significands (T = Q^n Q r_Q e^{-x}, D = x + T, r_D = D^{-1/2} by Newton
+    steps, D^{-s} = r_D (r_D^2)^n times c), so the FP64 pipe keeps Q~ and
+    the division.  In FP64 (int_newton False): Q^n, Q rsqrt(Q), and
+    rsqrt(D)^{2n+1} for n_top <= 13, else (1/D)^n (1/D) rsqrt(1/D)."""
     rec = _fits(53)[n_top]
     pw = square_multiply_ops(n_top)
     fma = root_product_ops(rec["u"]) + root_product_ops(rec["v"]) + 4  # Q~ (given u/v)
     if int_newton:
-        fma += pw + 1 + 1 + 1  # Q^n, times sqrt(Q), times e^{-x}, plus x
-        fma += pw + 2  # w^n, c r and the product
         return {"fma": fma, "div": 1, "sqrt": 0, "exp": 0, "rsqrt": 0}
     fma += pw + 1 + 1 + 1 + 1  # Q^n, Q rsqrt(Q), product, times e^{-x}, plus x
     if n_top <= 13:

@@ -124,16 +124,17 @@ def test_integer_recursion_threshold_matches_the_kernels():
 
 
 def test_closed_form_newton_steps_leave_the_fp64_pipe():
-    # Q rsqrt(Q) and D^{-1/2} (with its square) as integer Newton steps below
-    # n_max = 12 and in the two-point rows: no FP64 reciprocal square root is
-    # left, the division u/v stays; the FP64 form differs by exactly those and
-    # the products they replace
+    # below n_max = 12 and in the two-point rows everything after Q runs on
+    # integer significands (the powers, Q rsqrt(Q), e^{-x}, + x, D^{-1/2} by
+    # Newton steps): the FP64 pipe keeps Q~ and the division u/v; the FP64
+    # form adds both powers (square and multiply), seven products and sums,
+    # and the reciprocal square roots (and 1/D from n_top = 14 on)
     for n_top in (1, 9, 13, 14, 18, 40):
         c = roofline._closed_form_counts(n_top)
         c64 = roofline._closed_form_counts(n_top, False)
         assert c["rsqrt"] == 0 and c["div"] == 1
         assert c64["rsqrt"] == 2 and c64["div"] == (1 if n_top <= 13 else 2)
-        assert c64["fma"] - c["fma"] == 2  # Q rsqrt(Q), and rs^2 or w rsqrt(w)
+        assert c64["fma"] - c["fma"] == 2 * roofline.square_multiply_ops(n_top) + 7
     import re
 
     src = open(os.path.join(os.path.dirname(roofline.__file__), "csrc", "boys_f64.cuh")).read()

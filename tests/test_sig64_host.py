@@ -21,7 +21,18 @@ HEADER = os.path.join(HERE, "..", "paper_2504_07637_gb300", "csrc", "boys_sig64.
 HARNESS = r"""
 #include "boys_sig64.cuh"
 #include <cstdio>
+#include <utility>
 using namespace boys;
+template <int... N>
+void pow_all(uint64_t s0, int e0, std::integer_sequence<int, N...>) {
+  auto one = [&](auto n) {
+    uint64_t s = s0;
+    int e = e0;
+    sig64_pow<decltype(n)::value>(s, e);
+    std::printf("%llu %d ", (unsigned long long)s, e);
+  };
+  (one(std::integral_constant<int, N>{}), ...);
+}
 int main() {
   char op[8];
   unsigned long long a, b;
@@ -62,6 +73,19 @@ int main() {
       int es;
       sig64_rsqrt(xb, sb, s, es);
       std::printf("%llu %d\n", (unsigned long long)s, es);
+    } else if (op[0] == 'p') {  // p s e: s 2^(e - 63) to the powers 0 .. 40, as sig64_pow
+      unsigned long long sb;
+      std::scanf("%llu %d", &sb, &e);
+      pow_all(sb, e, std::make_integer_sequence<int, 41>{});
+      std::printf("\n");
+    } else if (op[0] == 's') {  // s sig e seed_bits: 1/sqrt of s 2^(e - 63) by sig64_rsqrt_sig
+      unsigned long long sb;
+      unsigned seed;
+      std::scanf("%llu %d %u", &sb, &e, &seed);
+      uint64_t s;
+      int es;
+      sig64_rsqrt_sig(sb, e, seed, s, es);
+      std::printf("%llu %d %u\n", (unsigned long long)s, es, sig64_rsqrt_seed_arg(sb, e));
     } else if (op[0] == 'k') {  // k x_bits: sig64_rsqrt_reduce
       unsigned long long xb;
       std::scanf("%llu", &xb);
@@ -288,6 +312,46 @@ def test_reciprocal_square_root_by_newton_steps(run):
         r = Fraction(s) * Fraction(2) ** (e - 63)
         # r^2 x = (1 + eps)^2: |eps| <= 2^-60 within |r^2 x - 1| <= 2^-59 + 2^-120
         assert abs(r * r * Fraction(float(x)) - 1) <= Fraction(1, 2**59) + Fraction(1, 2**120), x
+
+
+def test_powers_by_repeated_squaring(run):
+    """sig64_pow: x^n for n = 0 .. 40 (the closed form's Q^n_top and
+    w^n_top) within n 2^-62 relative of the exact power (each of its at most
+    2 log2(n) products truncates below 2^-62)."""
+    rng = np.random.default_rng(23)
+    cases = [(int(s) | 1 << 63, int(e)) for s, e in zip(rng.integers(0, 2**63, 60, dtype=np.uint64),
+                                                          rng.integers(-40, 40, 60))]
+    cases += [(1 << 63, 0), ((1 << 64) - 1, 3), ((1 << 63) + 1, -5)]
+    for (s0, e0), line in zip(cases, run([f"p {s} {e}" for s, e in cases])):
+        t = [int(v) for v in line.split()]
+        x = Fraction(s0) * Fraction(2) ** (e0 - 63)
+        for n in range(41):
+            s, e = t[2 * n], t[2 * n + 1]
+            assert 1 << 63 <= s < 1 << 64
+            got = Fraction(s) * Fraction(2) ** (e - 63)
+            assert abs(got / x**n - 1) <= Fraction(max(n, 1), 2**61), (s0, e0, n)
+
+
+def test_reciprocal_square_root_of_a_significand(run):
+    """sig64_rsqrt_sig on values s 2^(e - 63) of either exponent parity (D of
+    the closed form), seeded as the kernels seed it from sig64_rsqrt_seed_arg:
+    within 2^-60 of 1/sqrt."""
+    rng = np.random.default_rng(24)
+    cases = [(int(s) | 1 << 63, int(e)) for s, e in zip(rng.integers(0, 2**63, 3000, dtype=np.uint64),
+                                                          rng.integers(-300, 300, 3000))]
+    cases += [(1 << 63, 0), (1 << 63, 1), ((1 << 64) - 1, -1), ((1 << 64) - 1, 2)]
+    lines = []
+    for s, e in cases:
+        a = Fraction(s) * Fraction(2) ** ((e & 1) - 63)  # in [1, 4)
+        seed = np.float32(1.0 / math.sqrt(float(a)) * (1.0 + rng.uniform(-(2.0**-20), 2.0**-20)))
+        lines.append(f"s {s} {e} {_float_bits(seed)}")
+    for (s0, e0), line in zip(cases, run(lines)):
+        s, e, ab = (int(v) for v in line.split())
+        a = _float(ab)
+        assert 1.0 <= a < 4.0 and abs(Fraction(a) / (Fraction(s0) * Fraction(2) ** ((e0 & 1) - 63)) - 1) < Fraction(1, 2**23)
+        r = Fraction(s) * Fraction(2) ** (e - 63)
+        v = Fraction(s0) * Fraction(2) ** (e0 - 63)
+        assert abs(r * r * v - 1) <= Fraction(1, 2**59) + Fraction(1, 2**120), (s0, e0)
 
 
 def test_sqrt_pi_over_two_constant():
