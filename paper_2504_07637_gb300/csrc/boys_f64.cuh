@@ -37,6 +37,7 @@ namespace boys {
 
 // 2^(j/64), j = 0..63, for the exponential below
 static __constant__ double kExp2Frac64[64] = BOYS_EXP2_FRAC64;
+static __constant__ uint64_t kExp2Frac64Sig[64] = BOYS_EXP2_FRAC64_SIG;
 
 // Row index of a lane without a list entry (rows of carried entries may be negative).
 constexpr int kNoRow = INT_MIN;
@@ -81,6 +82,38 @@ __device__ __forceinline__ double exp_neg(double x, const double *__restrict__ t
   const double t = tab64[k & 63];
   const double res = fma(t, p, t);
   return __longlong_as_double(__double_as_longlong(res) + ((long long)(k >> 6) << 52));
+}
+
+// The exponential's tables in shared memory: 2^(j/64) as doubles (exp_neg)
+// and as 64-bit significands (sig64_exp_neg).
+struct F64ExpTab {
+  double d[64];
+  uint64_t s[64];
+};
+
+// e^{-x} as a double and as a 64-bit significand (s, e).  INT: by
+// sig64_exp_neg on the integer pipes (0 <= x < 128: the closed form's
+// arguments), rounded once to d; otherwise exp_neg in FP64, and (s, e) its
+// bits.  Tang's exponential costs about 9 DFMA times on the FP64 pipe
+// (f64_int_exp says where the integer form is used).
+struct F64E {
+  double d;
+  uint64_t s;
+  int e;
+};
+template <bool INT>
+__device__ __forceinline__ F64E f64_exp_neg_both(const double x, const F64ExpTab &tab) {
+  F64E r;
+  if constexpr (INT) {
+    sig64_exp_neg((uint64_t)__double_as_longlong(x), tab.s, r.s, r.e);
+    r.d = __longlong_as_double((long long)sig64_round_bits(r.s, r.e));
+  } else {
+    r.d = exp_neg(x, tab.d);
+    const uint64_t b = (uint64_t)__double_as_longlong(r.d);
+    r.s = sig64_of_bits(b);
+    r.e = exp_of_bits(b);
+  }
+  return r;
 }
 
 // The float approximation that seeds the Newton steps: one special-function
@@ -129,6 +162,16 @@ __device__ __forceinline__ bool sig64_to_double(const uint64_t s, const int e, d
 // requests of one order share their arithmetic bit for bit.
 __host__ __device__ constexpr bool f64_int_rsqrt(int n_max, bool two) { return two || n_max < 12; }
 
+// Whether e^{-x} comes from sig64_exp_neg (integer pipes) instead of the FP64
+// table method: for the one-point rows up to n_max = 5, where the FP64 pipe
+// binds hardest (n_max = 0: 36.4 -> 44.6 G values/s, 4: 141.9 -> 157.9, 5:
+// 163.2 -> 178.3).  Above, and in the two-point rows, the kernels are no
+// longer held by the FP64 pipe alone and the integer exponential measured
+// slower or no faster (n_max = 6: 178.6 -> 170.5, 7: 197.9 -> 198.7, 8:
+// 183.4 -> 180.3, 11: -0.6%, two-point n_max = 16: -1.7%, 36: +2.6%).  Again a
+// rule of the order only.
+__host__ __device__ constexpr bool f64_int_exp(int n_max, bool two) { return !two && n_max <= 5; }
+
 // F_NTOP(x) by the closed form of Eq. "fq", given e = e^{-x}.  Q~ (the root
 // products and u/v) and e^{-x} are FP64 either way.  INT: everything after
 // Q on 64-bit significands, rounded once at the end: T = Q^NTOP Q r_Q e^{-x}
@@ -154,7 +197,8 @@ __device__ __forceinline__ double f64_closed_form_tail_fp64(const double x, cons
 }
 
 template <int NTOP, bool INT>
-__device__ __forceinline__ double f64_closed_form(const double x, const double e) {
+__device__ __forceinline__ double f64_closed_form(const double x, const F64E &ex) {
+  const double e = ex.d;
   using Tab = BoysF64<NTOP>;
   double u, v;
   Tab::uv(x, u, v);
@@ -163,7 +207,7 @@ __device__ __forceinline__ double f64_closed_form(const double x, const double e
   const double q = fma(p, r, fma(Tab::kQ1, x, Tab::kQ0));
   if constexpr (INT) {
     if (q > 0.0 && f64_is_normal(q) && f64_is_normal(e)) {
-      const uint64_t qb = (uint64_t)__double_as_longlong(q), ebits = (uint64_t)__double_as_longlong(e);
+      const uint64_t qb = (uint64_t)__double_as_longlong(q);
       const uint64_t sq = sig64_of_bits(qb);
       const int eq = exp_of_bits(qb);
       uint64_t sr, st = sq;
@@ -172,7 +216,7 @@ __device__ __forceinline__ double f64_closed_form(const double x, const double e
       sig64_pow<NTOP>(st, et);   // Q^NTOP
       sig64_mul(st, et, sq, eq);
       sig64_mul(st, et, sr, er);  // Q^(NTOP + 1/2)
-      sig64_mul(st, et, sig64_of_bits(ebits), exp_of_bits(ebits));
+      sig64_mul(st, et, ex.s, ex.e);
       if (f64_is_normal(x)) {  // D = x + T (x >= 0; zero and subnormal x add nothing)
         const uint64_t xb = (uint64_t)__double_as_longlong(x);
         sig64_add(st, et, sig64_of_bits(xb), exp_of_bits(xb));
@@ -224,14 +268,14 @@ static __constant__ Sig64Tab kHalfOddTab = make_sig64_tab(false);
 struct Sig64Down {
   uint64_t sf, sx, se;
   int ef, ex, ee;
-  __device__ __forceinline__ void start(const double f, const double tx, const double e) {
-    const uint64_t fb = __double_as_longlong(f), xb = __double_as_longlong(tx), eb = __double_as_longlong(e);
+  __device__ __forceinline__ void start(const double f, const double tx, const F64E &e) {
+    const uint64_t fb = __double_as_longlong(f), xb = __double_as_longlong(tx);
     sf = sig64_of_bits(fb);
     ef = exp_of_bits(fb);
     sx = sig64_of_bits(xb);
     ex = exp_of_bits(xb);
-    se = sig64_of_bits(eb);
-    ee = exp_of_bits(eb);
+    se = e.s;
+    ee = e.e;
   }
   // F_{M-1} from F_M
   template <int M>
@@ -267,12 +311,12 @@ __host__ __device__ constexpr bool f64_int_recursion(int steps) { return steps <
 // Eq. "r" from F_TOP (in f) down to F_LO, storing F_m for m <= NMAX: on the
 // integer pipes (INT), else in FP64.
 template <int TOP, int LO, int NMAX, bool INT = f64_int_recursion(TOP - LO)>
-__device__ __forceinline__ void f64_recurse(double f, const double tx, const double e, double (&F)[NMAX + 1]) {
+__device__ __forceinline__ void f64_recurse(double f, const double tx, const F64E &e, double (&F)[NMAX + 1]) {
   if constexpr (!INT) {
 #pragma unroll
     for (int m = TOP; m > LO; --m) {
       if (m <= NMAX) F[m] = f;
-      f = fma(tx, f, e) * (1.0 / double(2 * m - 1));
+      f = fma(tx, f, e.d) * (1.0 / double(2 * m - 1));
     }
     if (LO <= NMAX) F[LO] = f;
   } else {
@@ -290,9 +334,10 @@ __device__ __forceinline__ void f64_recurse(double f, const double tx, const dou
 }
 
 template <int NTOP, int NMAX>
-__device__ __forceinline__ void f64_formula(const double x, double (&F)[NMAX + 1], const double *__restrict__ tab64) {
-  const double e = exp_neg(x, tab64);
-  f64_recurse<NTOP, 0, NMAX>(f64_closed_form<NTOP, f64_int_rsqrt(NMAX, false)>(x, e), twice(x), e, F);
+__device__ __forceinline__ void f64_formula(const double x, double (&F)[NMAX + 1], const F64ExpTab &tab) {
+  constexpr bool INT = f64_int_rsqrt(NMAX, false);
+  const F64E e = f64_exp_neg_both<f64_int_exp(NMAX, false)>(x, tab);
+  f64_recurse<NTOP, 0, NMAX>(f64_closed_form<NTOP, INT>(x, e), twice(x), e, F);
 }
 
 // Order n_bar of the two-point evaluation: the lower half of the orders.
@@ -303,11 +348,10 @@ __host__ __device__ constexpr int f64_two_point_nbar(int n_max) { return n_max /
 // each and one shared e^{-x}; the low orders then carry the error of a short
 // recursion from a low order instead of a long one from the top.
 template <int NTOP, int NTOP_LO, int NBAR, int NMAX>
-__device__ __forceinline__ void f64_formula_two(const double x, double (&F)[NMAX + 1],
-                                                const double *__restrict__ tab64) {
+__device__ __forceinline__ void f64_formula_two(const double x, double (&F)[NMAX + 1], const F64ExpTab &tab) {
   static_assert(NBAR < NMAX && NTOP_LO >= NBAR && NTOP_LO < NTOP, "orders");
   constexpr bool INT = f64_int_recursion(NTOP - NBAR - 1 + NTOP_LO);
-  const double e = exp_neg(x, tab64);
+  const F64E e = f64_exp_neg_both<f64_int_exp(NMAX, true)>(x, tab);
   const double tx = twice(x);
   f64_recurse<NTOP, NBAR + 1, NMAX, INT>(f64_closed_form<NTOP, true>(x, e), tx, e, F);
   double lo[NBAR + 1];
@@ -480,7 +524,7 @@ __device__ __forceinline__ void f64_stage_flush(double *__restrict__ out, const 
 // reached (orders above HI of that chunk were staged before, by the other
 // recursion of a two-point evaluation).  The arithmetic is f64_recurse's.
 template <int TOP, int LO, int HI, int W, int CH, int K, bool INT>
-__device__ __forceinline__ void f64_recurse_staged(const double (&f0)[K], const double (&tx)[K], const double (&e)[K],
+__device__ __forceinline__ void f64_recurse_staged(const double (&f0)[K], const double (&tx)[K], const F64E (&e)[K],
                                                    const int (&j)[K], double *__restrict__ out,
                                                    double *__restrict__ stg, const int lane) {
   if constexpr (!INT) {
@@ -496,7 +540,7 @@ __device__ __forceinline__ void f64_recurse_staged(const double (&f0)[K], const 
       }
       if constexpr (m > LO) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) f[k] = fma(tx[k], f[k], e[k]) * (1.0 / double(2 * m - 1));
+        for (int k = 0; k < K; ++k) f[k] = fma(tx[k], f[k], e[k].d) * (1.0 / double(2 * m - 1));
       }
     });
   } else {
@@ -576,15 +620,17 @@ __device__ __forceinline__ void f64_recurse_staged(const double (&f0)[K], const 
 // as above; the arithmetic is theirs.
 template <int NTOP, int NMAX, int CH, int K, bool TWO>
 __device__ __forceinline__ void f64_formula_staged(const double (&x)[K], const int (&j)[K], double *__restrict__ out,
-                                                   double *__restrict__ stg, const double *__restrict__ tab64,
+                                                   double *__restrict__ stg, const F64ExpTab &tab,
                                                    const int lane) {
   constexpr int W = NMAX + 1;
-  double e[K], tx[K], f[K];
+  constexpr bool INTE = f64_int_rsqrt(NMAX, TWO);
+  F64E e[K];
+  double tx[K], f[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    e[k] = exp_neg(x[k], tab64);
+    e[k] = f64_exp_neg_both<f64_int_exp(NMAX, TWO)>(x[k], tab);
     tx[k] = twice(x[k]);
-    f[k] = f64_closed_form<NTOP, f64_int_rsqrt(NMAX, TWO)>(x[k], e[k]);
+    f[k] = f64_closed_form<NTOP, INTE>(x[k], e[k]);
   }
   if constexpr (!TWO) {
     f64_recurse_staged<NTOP, 0, NMAX, W, CH, K, true>(f, tx, e, j, out, stg, lane);
@@ -813,7 +859,7 @@ template <int TILE, bool CARRY = false>
 struct F64TileSmem : F64Carry<CARRY> {
   double xs[TILE];
   unsigned short lst[TILE];  // below list from the front, above list from the back
-  double tab64[64];
+  F64ExpTab tab;
   int cnt[2], next[2];
 };
 
@@ -967,7 +1013,7 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
           j[k] = kNoRow;
           if (q + 32 * k < flo) j[k] = entry(0, q + 32 * k, xv[k]);
         }
-        f64_formula_staged<NTOP, NMAX, STAGE, ILP, TWO>(xv, j, epi.out, stg, sm.tab64, lane);
+        f64_formula_staged<NTOP, NMAX, STAGE, ILP, TWO>(xv, j, epi.out, stg, sm.tab, lane);
         continue;
       }
       if constexpr (ILP == 2) {
@@ -975,8 +1021,8 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
           double xa, xb;
           const int ja = entry(0, q, xa), jb = entry(0, q + 32, xb);
           double Fa[W], Fb[W];
-          f64_formula<NTOP, NMAX>(xa, Fa, sm.tab64);
-          f64_formula<NTOP, NMAX>(xb, Fb, sm.tab64);
+          f64_formula<NTOP, NMAX>(xa, Fa, sm.tab);
+          f64_formula<NTOP, NMAX>(xb, Fb, sm.tab);
           epi(ja, Fa);
           epi(jb, Fb);
           continue;
@@ -988,9 +1034,9 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
         double F[W];
         if constexpr (TWO) {
           constexpr int NBAR = f64_two_point_nbar(NMAX);
-          f64_formula_two<NTOP, f64_top_order(NBAR), NBAR, NMAX>(xq, F, sm.tab64);
+          f64_formula_two<NTOP, f64_top_order(NBAR), NBAR, NMAX>(xq, F, sm.tab);
         } else {
-          f64_formula<NTOP, NMAX>(xq, F, sm.tab64);
+          f64_formula<NTOP, NMAX>(xq, F, sm.tab);
         }
         epi(j, F);
       }
@@ -1096,7 +1142,10 @@ __device__ __forceinline__ void f64_tile(const double *__restrict__ xt, int nel,
 
 template <int BLOCK, typename Smem>
 __device__ __forceinline__ void f64_load_table(Smem &sm) {
-  for (int i = threadIdx.x; i < 64; i += BLOCK) sm.tab64[i] = kExp2Frac64[i];
+  for (int i = threadIdx.x; i < 64; i += BLOCK) {
+    sm.tab.d[i] = kExp2Frac64[i];
+    sm.tab.s[i] = kExp2Frac64Sig[i];
+  }
   if (threadIdx.x == 0) sm.cn[0] = sm.cn[1] = 0;  // nothing carried yet
 }
 

@@ -168,6 +168,62 @@ BOYS_HD void sig64_pow(uint64_t &s, int &e) {
   }
 }
 
+// The high 64 bits of a 64 x 64-bit product, unsigned and signed (floor).
+BOYS_HD uint64_t mulhi_u64(uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+  return __umul64hi(a, b);
+#else
+  return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+BOYS_HD int64_t mulhi_s64(int64_t a, int64_t b) {
+#if defined(__CUDA_ARCH__)
+  return __mul64hi(a, b);
+#else
+  return (int64_t)(((__int128)a * b) >> 64);
+#endif
+}
+
+// e^{-x} for 0 <= x < 128 as a Sig64, by Tang's table-driven method in 64-bit
+// fixed point:
+//   X = x 2^57 (exact for x >= 2^-5, else within 2^-57; 0 below 2^-57),
+//   k = round(x 64/ln2), r = x - k ln2/64 (|r| <= ln2/128 plus 2^-50):
+//   R = X - k Lh - (k Ll) 2^-64, with ln2/64 2^57 = Lh + Ll 2^-64,
+//   e^{-r} = sum_{i<=6} (-r)^i / i! by Horner on 2^62-scaled coefficients
+//   (the first term left out is below 2^-65; each step truncates 2^-62),
+//   e^{-x} = 2^q 2^(j/64) e^{-r} with -k = 64 q + j, 2^(j/64) from tab (the
+//   64-bit significands round(2^(j/64) 2^63)).
+// The error is below 2^-55 relative (R within 1.5 units of 2^-57).
+constexpr uint64_t kExpInvL = 0xb8aa3b295c17f0bcull;  // round(64/ln2 2^57)
+constexpr uint64_t kExpLh = 0x58b90bfbe8e7bull;       // floor(ln2/64 2^57)
+constexpr uint64_t kExpLl = 0xcd5e4f1d9cc01f98ull;    // its remainder 2^64, rounded
+// round((-1)^i / i! 2^62), i = 0..6
+constexpr int64_t kExpA0 = 4611686018427387904ll, kExpA1 = -4611686018427387904ll, kExpA2 = 2305843009213693952ll,
+                  kExpA3 = -768614336404564651ll, kExpA4 = 192153584101141163ll, kExpA5 = -38430716820228233ll,
+                  kExpA6 = 6405119470038039ll;
+BOYS_HD void sig64_exp_neg(uint64_t xbits, const uint64_t *tab, uint64_t &s, int &e) {
+  const int ex = exp_of_bits(xbits);  // -1023 for 0 and subnormals
+  const int sh = 6 - ex;
+  const uint64_t X = sh < 64 ? sig64_of_bits(xbits) >> sh : 0ull;
+  const int64_t k = (int64_t)((mulhi_u64(X, kExpInvL) + (1ull << 49)) >> 50);
+  const int64_t R = (int64_t)(X - (uint64_t)k * kExpLh - mulhi_u64((uint64_t)k, kExpLl));
+  const int64_t R7 = R * 128;  // r 2^64 (|R| < 2^50)
+  int64_t acc = kExpA5 + mulhi_s64(R7, kExpA6);
+  acc = kExpA4 + mulhi_s64(R7, acc);
+  acc = kExpA3 + mulhi_s64(R7, acc);
+  acc = kExpA2 + mulhi_s64(R7, acc);
+  acc = kExpA1 + mulhi_s64(R7, acc);
+  acc = kExpA0 + mulhi_s64(R7, acc);
+  // acc = e^{-r} 2^62 in (2^61, 2^63)
+  const bool hi = acc >= (int64_t)(1ull << 62);
+  const uint64_t sq = hi ? (uint64_t)acc << 1 : (uint64_t)acc << 2;
+  const int64_t nk = -k;
+  s = tab[nk & 63];
+  e = 0;
+  sig64_mul(s, e, sq, hi ? 0 : -1);
+  e += (int)(nk >> 6);
+}
+
 // c_0 = sqrt(pi)/2 (Eq. "limf1": F_0 = c_0 / sqrt(x) above the cut-off),
 // rounded to 64 bits: 0.886226925452758013649... = 0xe2dfc48da77b553d 2^-64.
 constexpr uint64_t kSig64C0s = 0xe2dfc48da77b553dull;

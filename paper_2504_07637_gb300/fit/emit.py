@@ -118,6 +118,8 @@ def emit_f64(table: dict) -> str:
     out += [
         "// 2^(j/64), j = 0..63 (table of the exponential used by the kernels)",
         f"#define BOYS_EXP2_FRAC64 {{{exp2_table()}}}",
+        "// the same as 64-bit significands: round(2^(j/64) 2^63) (the integer exponential)",
+        f"#define BOYS_EXP2_FRAC64_SIG {{{exp2_table_sig()}}}",
         f"static const double kBoysF64CutoffHost[{nmax + 1}] = {{" + ", ".join(host_z) + "};",
         f"static const double kBoysCHost[{nmax + 1}] = {{" + ", ".join(host_c) + "};",
         f"static const float kBoysF64FitBitsHost[{nmax + 1}] = {{" + ", ".join(e + "f" for e in host_eps) + "};",
@@ -264,6 +266,19 @@ def exp2_table_ff(n: int = 32) -> str:
     for j in range(n):
         hi, lo = f_split(str(Decimal(2) ** (Decimal(j) / Decimal(n))))
         vals.append(f"{hi}, {lo}")
+    return ", ".join(vals)
+
+
+def exp2_table_sig(n: int = 64) -> str:
+    """round(2^(j/n) 2^63), j = 0..n-1: 2^(j/n) as a 64-bit significand of
+    exponent 0, correctly rounded."""
+    from decimal import ROUND_HALF_EVEN, Decimal, getcontext
+
+    getcontext().prec = 80
+    vals = []
+    for j in range(n):
+        v = (Decimal(2) ** (Decimal(j) / Decimal(n))) * (Decimal(2) ** 63)
+        vals.append(f"0x{int(v.to_integral_value(rounding=ROUND_HALF_EVEN)):016x}ull")
     return ", ".join(vals)
 
 

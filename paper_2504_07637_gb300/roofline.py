@@ -4,8 +4,9 @@ Counts follow the method (Sec. 2) as the double kernels evaluate it: below the
 cut-off one evaluation of Q~ in root-product form, one division u/v, one
 exponential (shared with the recursion, Eq. "r"), the half-integer powers
 Q^{n+1/2} and D^{-(n+1/2)} as square-and-multiply plus a reciprocal square
-root each (below n_max = 12 and in the two-point rows the kernels take the
-reciprocal square roots from Newton steps on 64-bit integer significands),
+root each (below n_max = 12 and in the two-point rows the kernels take
+everything after Q~, and up to n_max = 5 the exponential, from 64-bit
+integer significands),
 and two operations per step of
 the downward recursion (on the integer pipes instead in the row kernels, and
 for recursions of up to 18 steps elsewhere); above it (Eq. "limf1") nothing
@@ -55,6 +56,13 @@ def int_rsqrt(n_max: int, two_point: bool = False) -> bool:
 
 
 INT_RSQRT_BELOW = 12
+INT_EXP_UPTO = 5
+
+
+def int_exp(n_max: int, two_point: bool = False) -> bool:
+    """Whether e^{-x} runs on the integer pipes (f64_int_exp in
+    csrc/boys_f64.cuh): the one-point rows up to n_max = 5."""
+    return not two_point and n_max <= INT_EXP_UPTO
 
 
 def _closed_form_counts(n_top: int, int_newton: bool = True) -> dict:
@@ -134,7 +142,7 @@ def f64_counts(n_max: int, n_top: int, int_chain: bool = True, rows: bool = True
     int_chain False, the recursion and the asymptote's chain are both
     counted in FP64 (the all-FP64 kernel)."""
     below = _closed_form_counts(n_top, int_chain and int_rsqrt(n_max))
-    below["exp"] = 1
+    below["exp"] = 0 if int_chain and int_exp(n_max) else 1  # else on the integer pipes
     if not (int_chain and int_recursion(n_top, n_max if rows else None)):
         below["fma"] += 2 * n_top  # recursion
     return below, _asymptote_counts(n_max, int_chain)

@@ -86,6 +86,14 @@ int main() {
       int es;
       sig64_rsqrt_sig(sb, e, seed, s, es);
       std::printf("%llu %d %u\n", (unsigned long long)s, es, sig64_rsqrt_seed_arg(sb, e));
+    } else if (op[0] == 'E') {  // E x_bits: e^{-x} by sig64_exp_neg
+      unsigned long long xb;
+      std::scanf("%llu", &xb);
+      static const uint64_t tab[64] = BOYS_EXP2_FRAC64_SIG;
+      uint64_t s;
+      int es;
+      sig64_exp_neg(xb, tab, s, es);
+      std::printf("%llu %d\n", (unsigned long long)s, es);
     } else if (op[0] == 'k') {  // k x_bits: sig64_rsqrt_reduce
       unsigned long long xb;
       std::scanf("%llu", &xb);
@@ -142,7 +150,10 @@ def run(tmp_path_factory):
         pytest.skip("no host C++ compiler")
     d = tmp_path_factory.mktemp("sig64")
     src = d / "h.cpp"
-    src.write_text(HARNESS)
+    # the exponential's table of 64-bit significands, from the generated coefficient header
+    inc = open(os.path.join(os.path.dirname(HEADER), "boys_coeffs_f64.inc")).read()
+    tab = next(line for line in inc.splitlines() if line.startswith("#define BOYS_EXP2_FRAC64_SIG "))
+    src.write_text(tab + "\n" + HARNESS)
     exe = d / "h"
     subprocess.run([cxx, "-O2", "-std=c++17", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
 
@@ -386,3 +397,41 @@ def test_integer_asymptote_against_the_oracle(run, oracle_mod, n):
     rel = (np.abs(got - ref) / ref).astype(np.float64)
     bound = (2.0 + np.arange(0, n + 1) / 32.0) * 2.0**-53
     assert np.all(rel.max(axis=0) <= bound), (rel.max(axis=0) / 2.0**-53)
+
+
+def _exp2_sig_table():
+    import re
+
+    inc = open(os.path.join(os.path.dirname(HEADER), "boys_coeffs_f64.inc")).read()
+    line = next(line for line in inc.splitlines() if line.startswith("#define BOYS_EXP2_FRAC64_SIG "))
+    return [int(v, 16) for v in re.findall(r"0x([0-9a-f]+)ull", line)]
+
+
+def test_exp2_significand_table_is_correctly_rounded():
+    # s_j = round(2^(j/64) 2^63): (s_j -+ 1/2)^64 brackets 2^(j + 64*63) exactly
+    tab = _exp2_sig_table()
+    assert len(tab) == 64 and tab[0] == 1 << 63
+    for j, s in enumerate(tab):
+        assert 1 << 63 <= s < 1 << 64
+        target = 1 << (j + 64 * 63)
+        assert (2 * s - 1) ** 64 <= target * 2**64 <= (2 * s + 1) ** 64, j
+
+
+def test_integer_exponential_against_mpmath(run):
+    """sig64_exp_neg (Tang's method in 64-bit fixed point) on [0, 128): within
+    2^-55 relative of e^{-x} (the closed form's arguments stay below 120), at
+    zero, subnormals, the reduction's edges (x near (k + 1/2) ln2/64) and the
+    fixed point's (x near 2^-57 and 2^-5)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 120
+    rng = np.random.default_rng(25)
+    xs = list(np.exp(rng.uniform(math.log(1e-30), math.log(127.9), 3000))) + list(rng.uniform(0.0, 127.99, 3000))
+    half = math.log(2) / 128
+    xs += [(2 * k + 1) * half * (1 + d) for k in (0, 1, 63, 64, 5000, 11000) for d in (-1e-15, 0.0, 1e-15)]
+    xs += [0.0, 5e-324, 2.2250738585072014e-308, 2.0**-61, 2.0**-57, 2.0**-56, 2.0**-5, 0.03125 * (1 - 2.0**-52),
+           1.0, 60.0, 118.0, 127.99]
+    got = [tuple(int(t) for t in line.split()) for line in run([f"E {_bits(x)}" for x in xs])]
+    for x, (s, e) in zip(xs, got):
+        assert 1 << 63 <= s < 1 << 64
+        v = mpmath.mpf(s) * mpmath.mpf(2) ** (e - 63)
+        assert abs(v / mpmath.exp(-mpmath.mpf(x)) - 1) <= mpmath.mpf(2) ** -55, x
