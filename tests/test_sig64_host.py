@@ -20,9 +20,46 @@ HEADER = os.path.join(HERE, "..", "paper_2504_07637_gb300", "csrc", "boys_sig64.
 
 HARNESS = r"""
 #include "boys_sig64.cuh"
+#include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <utility>
 using namespace boys;
+// the closed form after Q as the kernels form it on the integer pipes (n_top
+// known at compile time): T = Q^n Q r_Q e^{-x}, D = x + T, r_D = D^{-1/2},
+// F = c r_D (r_D^2)^n, from doubles q, e, x, c (the seeds: float 1/sqrt)
+static uint32_t host_seed(uint32_t abits) {  // 1/sqrt(a) in float, a in [1, 4)
+  float a, r;
+  std::memcpy(&a, &abits, 4);
+  r = 1.0f / std::sqrt(a);
+  uint32_t rb;
+  std::memcpy(&rb, &r, 4);
+  return rb;
+}
+template <int N>
+uint64_t tail(uint64_t qb, uint64_t ebits, uint64_t xb, uint64_t cb) {
+  const uint64_t sq = sig64_of_bits(qb);
+  const int eq = exp_of_bits(qb);
+  uint64_t sr, st = sq;
+  int er, et = eq, k;
+  sig64_rsqrt(qb, host_seed(sig64_rsqrt_reduce(qb, k)), sr, er);
+  sig64_pow<N>(st, et);
+  sig64_mul(st, et, sq, eq);
+  sig64_mul(st, et, sr, er);
+  sig64_mul(st, et, sig64_of_bits(ebits), exp_of_bits(ebits));
+  if (((xb >> 52) & 0x7ff) != 0) sig64_add(st, et, sig64_of_bits(xb), exp_of_bits(xb));
+  uint64_t sd, sw;
+  int ed, ew;
+  sig64_rsqrt_sig(st, et, host_seed(sig64_rsqrt_seed_arg(st, et)), sd, ed);
+  sw = sd;
+  ew = ed;
+  sig64_mul(sw, ew, sd, ed);
+  sig64_pow<N>(sw, ew);
+  sig64_mul(sw, ew, sd, ed);
+  sig64_mul(sw, ew, sig64_of_bits(cb), exp_of_bits(cb));
+  return sig64_round_bits(sw, ew);
+}
+
 template <int... N>
 void pow_all(uint64_t s0, int e0, std::integer_sequence<int, N...>) {
   auto one = [&](auto n) {
@@ -94,6 +131,19 @@ int main() {
       int es;
       sig64_exp_neg(xb, tab, s, es);
       std::printf("%llu %d\n", (unsigned long long)s, es);
+    } else if (op[0] == 'T') {  // T n q e x c: the closed form's integer tail
+      unsigned long long qb, eb2, xb, cb;
+      std::scanf("%d %llu %llu %llu %llu", &e, &qb, &eb2, &xb, &cb);
+      unsigned long long r = 0;
+      switch (e) {
+        case 1: r = tail<1>(qb, eb2, xb, cb); break;
+        case 5: r = tail<5>(qb, eb2, xb, cb); break;
+        case 9: r = tail<9>(qb, eb2, xb, cb); break;
+        case 13: r = tail<13>(qb, eb2, xb, cb); break;
+        case 20: r = tail<20>(qb, eb2, xb, cb); break;
+        case 40: r = tail<40>(qb, eb2, xb, cb); break;
+      }
+      std::printf("%llu\n", r);
     } else if (op[0] == 'k') {  // k x_bits: sig64_rsqrt_reduce
       unsigned long long xb;
       std::scanf("%llu", &xb);
@@ -435,3 +485,31 @@ def test_integer_exponential_against_mpmath(run):
         assert 1 << 63 <= s < 1 << 64
         v = mpmath.mpf(s) * mpmath.mpf(2) ** (e - 63)
         assert abs(v / mpmath.exp(-mpmath.mpf(x)) - 1) <= mpmath.mpf(2) ** -55, x
+
+
+@pytest.mark.parametrize("n_top", [1, 5, 9, 13, 20, 40])
+def test_integer_closed_form_tail_against_mpmath(run, n_top):
+    """The closed form after Q (Eq. "fq") as the kernels form it on the integer
+    pipes: F = c (x + Q^s e)^{-s}, s = n_top + 1/2, from the doubles Q, e, x
+    and c, with the powers, Q rsqrt(Q), D = x + T and D^{-1/2} on 64-bit
+    significands and one rounding at the end.  About 2 s truncations of at
+    most 2^-62 in T and in D^{-s}, amplified by the power s, and the final
+    rounding: within 1 + s^2/256 units of 2^-53 of the exact value.  Q is drawn
+    around the value that gives F_{n_top}(0) = 1/(2 n_top + 1), x over the
+    range below the cut-off."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 150
+    rng = np.random.default_rng(300 + n_top)
+    s = n_top + 0.5
+    c = math.gamma(s) / 2
+    q0 = (c * (2 * n_top + 1)) ** (1 / (s * s))
+    q = q0 * np.exp(rng.uniform(math.log(0.97), math.log(1.05), 600))
+    x = np.concatenate([[0.0, 5e-324], rng.uniform(0.0, 3 * n_top + 40, 598)])
+    e = np.exp(-x)
+    lines = [f"T {n_top} {_bits(a)} {_bits(b)} {_bits(xx)} {_bits(c)}" for a, b, xx in zip(q, e, x)]
+    got = [_double(int(v)) for v in run(lines)]
+    sm = mpmath.mpf(n_top) + mpmath.mpf(1) / 2
+    bound = (1 + s * s / 256) * mpmath.mpf(2) ** -53
+    for a, b, xx, g in zip(q, e, x, got):
+        ref = mpmath.mpf(c) * (mpmath.mpf(xx) + mpmath.mpf(a) ** sm * mpmath.mpf(b)) ** (-sm)
+        assert abs(mpmath.mpf(g) / ref - 1) <= bound, (n_top, a, xx)
