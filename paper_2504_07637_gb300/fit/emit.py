@@ -298,21 +298,31 @@ def exp2_table(n: int = 64) -> str:
 F32_SOURCE = "boys_fit_b24_plus1.json"
 
 
-def main():
+def render_f64() -> str:
+    """csrc/boys_coeffs_f64.inc from the committed 53-bit fits."""
     with open(os.path.join(COEFF_DIR, "boys_fit_b53.json")) as fh:
-        t53 = json.load(fh)
-    src = emit_f64(t53)
+        return emit_f64(json.load(fh))
+
+
+def render_f32() -> str | None:
+    """csrc/boys_coeffs_f32.inc from the committed float fits (None without them)."""
+    f32_path = os.path.join(COEFF_DIR, F32_SOURCE)
+    if not os.path.exists(f32_path):
+        return None
+    with open(f32_path) as fh:
+        src = emit_f32(json.load(fh), F32_SOURCE)
+    src += "\n// 2^(j/32), j = 0..31, as (hi, lo) float pairs\n"
+    src += f"#define BOYS_EXP2_FRAC32_FF {{{exp2_table_ff()}}}\n"
+    return src
+
+
+def main():
     path = os.path.join(CSRC, "boys_coeffs_f64.inc")
     with open(path, "w") as fh:
-        fh.write(src)
+        fh.write(render_f64())
     print(f"wrote {path}")
-    f32_path = os.path.join(COEFF_DIR, F32_SOURCE)
-    if os.path.exists(f32_path):
-        with open(f32_path) as fh:
-            t24 = json.load(fh)
-        src = emit_f32(t24, F32_SOURCE)
-        src += "\n// 2^(j/32), j = 0..31, as (hi, lo) float pairs\n"
-        src += f"#define BOYS_EXP2_FRAC32_FF {{{exp2_table_ff()}}}\n"
+    src = render_f32()
+    if src is not None:
         path = os.path.join(CSRC, "boys_coeffs_f32.inc")
         with open(path, "w") as fh:
             fh.write(src)
