@@ -165,12 +165,14 @@ __host__ __device__ constexpr bool f64_int_rsqrt(int n_max, bool two) { return t
 // Whether e^{-x} comes from sig64_exp_neg (integer pipes) instead of the FP64
 // table method: for the one-point rows up to n_max = 5, where the FP64 pipe
 // binds hardest (n_max = 0: 36.4 -> 44.6 G values/s, 4: 141.9 -> 157.9, 5:
-// 163.2 -> 178.3).  Above, and in the two-point rows, the kernels are no
-// longer held by the FP64 pipe alone and the integer exponential measured
-// slower or no faster (n_max = 6: 178.6 -> 170.5, 7: 197.9 -> 198.7, 8:
-// 183.4 -> 180.3, 11: -0.6%, two-point n_max = 16: -1.7%, 36: +2.6%).  Again a
-// rule of the order only.
-__host__ __device__ constexpr bool f64_int_exp(int n_max, bool two) { return !two && n_max <= 5; }
+// 163.2 -> 178.3), and from n_max = 12 on, whose closed form stays in FP64
+// (12: 207.0 -> 210.4, 16: 228.8 -> 235.7, 20 to 36: +0.1 to +0.4%).  From
+// n_max = 6 to 11, with the closed form's tail on the integer pipes, and in
+// the two-point rows the integer exponential measured slower or no faster
+// (n_max = 6: 178.6 -> 170.5, 7: 197.9 -> 198.7, 8: 183.4 -> 180.3, 11:
+// -0.6%, two-point n_max = 16: -1.7%, 36: +2.6%).  Again a rule of the order
+// only.
+__host__ __device__ constexpr bool f64_int_exp(int n_max, bool two) { return !two && (n_max <= 5 || n_max >= 12); }
 
 // F_NTOP(x) by the closed form of Eq. "fq", given e = e^{-x}.  Q~ (the root
 // products and u/v) and e^{-x} are FP64 either way.  INT: everything after

@@ -5,9 +5,8 @@ cut-off one evaluation of Q~ in root-product form, one division u/v, one
 exponential (shared with the recursion, Eq. "r"), the half-integer powers
 Q^{n+1/2} and D^{-(n+1/2)} as square-and-multiply plus a reciprocal square
 root each (below n_max = 12 and in the two-point rows the kernels take
-everything after Q~, and up to n_max = 5 the exponential, from 64-bit
-integer significands),
-and two operations per step of
+everything after Q~, and up to n_max = 5 and from n_max = 12 on the
+exponential, from 64-bit integer significands), and two operations per step of
 the downward recursion (on the integer pipes instead in the row kernels, and
 for recursions of up to 18 steps elsewhere); above it (Eq. "limf1") nothing
 on the FP64 pipe: F_0 and
@@ -61,8 +60,9 @@ INT_EXP_UPTO = 5
 
 def int_exp(n_max: int, two_point: bool = False) -> bool:
     """Whether e^{-x} runs on the integer pipes (f64_int_exp in
-    csrc/boys_f64.cuh): the one-point rows up to n_max = 5."""
-    return not two_point and n_max <= INT_EXP_UPTO
+    csrc/boys_f64.cuh): the one-point rows up to n_max = 5 and from
+    n_max = 12 on."""
+    return not two_point and (n_max <= INT_EXP_UPTO or n_max >= INT_RSQRT_BELOW)
 
 
 def _closed_form_counts(n_top: int, int_newton: bool = True) -> dict:

@@ -73,7 +73,7 @@ def test_contraction_counts():
     for n_max, n_top in ((0, 0), (8, 9), (16, 18)):
         row_b, row_a = roofline.f64_counts(n_max, n_top)
         b, a = roofline.f64_counts_contract(n_max, n_top, uniform=True)
-        assert b["fma"] == row_b["fma"] + n_max + 1 and b["exp"] == (0 if n_max <= 5 else 1)
+        assert b["fma"] == row_b["fma"] + n_max + 1 and b["exp"] == (0 if n_max <= 5 or n_max >= 12 else 1)
         assert a["fma"] == n_max + 1 and a["rsqrt"] == 0 and a["div"] == 0
         _, a64 = roofline.f64_counts_contract(n_max, n_top, uniform=True, int_chain=False)
         assert a64["fma"] == n_max + 2 + (1 if 1 <= n_max <= 12 else 0) and a64["rsqrt"] == 1
@@ -151,10 +151,10 @@ def test_integer_exponential_rule_matches_the_kernels():
     import re
 
     src = open(os.path.join(os.path.dirname(roofline.__file__), "csrc", "boys_f64.cuh")).read()
-    m = re.search(r"constexpr bool f64_int_exp\(int n_max, bool two\) \{ return !two && n_max <= (\d+); \}", src)
-    assert m and int(m.group(1)) == roofline.INT_EXP_UPTO
-    for n_max in (0, 5, 6, 16):
+    m = re.search(r"constexpr bool f64_int_exp\(int n_max, bool two\) \{ return !two && \(n_max <= (\d+) \|\| n_max >= (\d+)\); \}", src)
+    assert m and int(m.group(1)) == roofline.INT_EXP_UPTO and int(m.group(2)) == roofline.INT_RSQRT_BELOW
+    for n_max in (0, 5, 6, 11, 12, 16, 36):
         b, _ = roofline.f64_counts(n_max, n_max + 1)
-        assert b["exp"] == (0 if n_max <= 5 else 1)
+        assert b["exp"] == (0 if n_max <= 5 or n_max >= 12 else 1)
     two, _ = roofline.f64_counts_two_point(16, 18, 8, 9)
     assert two["exp"] == 1
