@@ -789,10 +789,13 @@ def measure_scale(wl, steps, warmup, device, seed, rates=None, e2e=False, clocks
             int_rec = roofline.int_recursion(n_top, n_max)
         rec_note = ("and the downward recursion run on the integer pipes and are not counted" if int_rec else
                     "runs on the integer pipes and is not counted; the downward recursion stays in FP64")
-        if roofline.int_rsqrt(n_max, bool(wl.get("two_point"))):
-            rec_note += "; so do F_0 = c_0/sqrt(x), 1/x and the closed form's reciprocal square roots (Newton steps)"
+        two = bool(wl.get("two_point"))
+        if roofline.int_rsqrt(n_max, two):
+            rec_note += "; so do F_0 = c_0/sqrt(x), 1/x and the closed form after Q (Newton steps)"
         else:
             rec_note += "; so do F_0 = c_0/sqrt(x) and 1/x (Newton steps)"
+        if roofline.int_exp(n_max, two):
+            rec_note += " and e^{-x} (64-bit fixed point)"
         achieved = t_arg * rates["fma"] * count / (ms / 1e3) / 1e12
         achieved64 = t_per_arg(False) * rates["fma"] * count / (ms / 1e3) / 1e12
         peak = rates["fma"] / 1e12
